@@ -38,13 +38,13 @@
  *       antisymmetric and momentum is conserved exactly).  v predicts the
  *       trapezoidal velocity u = j/n + g/2 + C/(2n), in which C depends on u
  *       itself, by a lagged linear-implicit step:
- *         (I + kappa H) v = j/n + g/2 + C_prev/(2n) + kappa H v_prev,
- *         H = (beta/2) T_prev,  T = sum_e w g2 n(r+e) khat khat^T,
- *       with C_prev, T_prev, v_prev from the previous step (zero, zero and the
- *       initial velocity at the first step) and kappa = 3/2.  At a steady
- *       state v = u exactly.  H is the local (diagonal) part of the viscous
- *       force's dependence on u(r); treating it implicitly keeps the
- *       collisional viscosity stable at liquid densities.
+ *         (1 + H) v = j/n + g/2 + C_prev/(2n) + H v_prev,
+ *         H = kappa (beta/2) t_prev / 3,  t = sum_e w g2 n(r+e),
+ *       with C_prev, t_prev, v_prev from the previous step (zero, zero and the
+ *       initial velocity at the first step) and kappa = 2.  At a steady state
+ *       v = u exactly.  beta t / 3 is the isotropic part of the local
+ *       (diagonal) dependence of F^viscous on u(r); treating it implicitly
+ *       keeps the collisional viscosity stable at liquid densities.
  *   R8  walls: nodes z = 0 and z = nz-1 are solid (n = 0 there, also beyond
  *       them); half-way bounce-back; x and y (and z without walls) periodic.
  *   R9  omega: constant 1/tau, or tau(r) - 1/2 scaled by
@@ -57,7 +57,7 @@
 
 #define Q 19
 static const double CS2 = 1.0 / 3.0;            /* R6 */
-static const double KAPPA = 1.5;                /* R7 */
+static const double KAPPA = 2.0;                /* R7 */
 
 /* ---------------------------------------------------------------------- */
 /* D3Q19 velocity set (Sec. 5): rest, six face and twelve edge neighbours.   */
@@ -173,9 +173,9 @@ typedef struct {
     double *nbar;                      /* [N] */
     double *Cf, *A;                    /* C[3][N], A[6][N] of this step */
     double *Cprev;                     /* [3][N] */
-    double *Tprev;                     /* shell tensor T of the previous step [6][N] */
+    double *Tprev;                     /* t = sum_e w g2 n(r+e) of the previous step [N] */
     double *vprev;                     /* field velocity of the previous step [3][N] */
-    double *Tcur;                      /* shell tensor T of this step [6][N] */
+    double *Tcur;                      /* t of this step [N] */
     long steps;
     int unstable;
 } wo_state;
@@ -237,9 +237,9 @@ wo_state *wo_create(int nx, int ny, int nz, int walls, double sigma, double tau,
     s->Cf = (double *)calloc(3 * N, sizeof(double));
     s->A = (double *)calloc(6 * N, sizeof(double));
     s->Cprev = (double *)calloc(3 * N, sizeof(double));
-    s->Tprev = (double *)calloc(6 * N, sizeof(double));
+    s->Tprev = (double *)calloc(N, sizeof(double));
     s->vprev = (double *)calloc(3 * N, sizeof(double));
-    s->Tcur = (double *)calloc(6 * N, sizeof(double));
+    s->Tcur = (double *)calloc(N, sizeof(double));
     return s;
 }
 
@@ -266,7 +266,7 @@ int wo_init(wo_state *s, const double *n0, const double *u0)
                 for (int q = 0; q < Q; q++) s->f[q * N + i] = feq(q, n, u);
             }
     memset(s->Cprev, 0, sizeof(double) * 3 * N);
-    memset(s->Tprev, 0, sizeof(double) * 6 * N);
+    memset(s->Tprev, 0, sizeof(double) * N);
     for (long i = 0; i < N; i++) {
         int z = (int)(i / ((long)s->nx * s->ny));
         for (int d = 0; d < 3; d++) s->vprev[d * N + i] = is_wall(s, z) ? 0.0 : u0[d * N + i];
@@ -274,22 +274,6 @@ int wo_init(wo_state *s, const double *n0, const double *u0)
     s->steps = 0;
     s->unstable = 0;
     return 0;
-}
-
-/* Solve the 3x3 system M x = r by Cramer's rule. */
-static void solve3(const double M[3][3], const double r[3], double x[3])
-{
-    double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1])
-               - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])
-               + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
-    for (int c = 0; c < 3; c++) {
-        double Mc[3][3];
-        for (int a = 0; a < 3; a++)
-            for (int b = 0; b < 3; b++) Mc[a][b] = (b == c) ? r[a] : M[a][b];
-        x[c] = (Mc[0][0] * (Mc[1][1] * Mc[2][2] - Mc[1][2] * Mc[2][1])
-              - Mc[0][1] * (Mc[1][0] * Mc[2][2] - Mc[1][2] * Mc[2][0])
-              + Mc[0][2] * (Mc[1][0] * Mc[2][1] - Mc[1][1] * Mc[2][0])) / det;
-    }
 }
 
 /* Step 4 of Sec. 5 / Eq. colonna: n = sum_q f_q, j = sum_q f_q c_q and the
@@ -315,21 +299,13 @@ static void moments(wo_state *s)
                 s->n[i] = n;
                 double beta = 2.0 * s->sigma * s->sigma * sqrt(CS2 / M_PI);
                 double h = 0.5 * beta * KAPPA;
-                const double *T6 = s->Tprev;
-                double H[3][3] = {{h * T6[0 * N + i], h * T6[3 * N + i], h * T6[4 * N + i]},
-                                  {h * T6[3 * N + i], h * T6[1 * N + i], h * T6[5 * N + i]},
-                                  {h * T6[4 * N + i], h * T6[5 * N + i], h * T6[2 * N + i]}};
-                double M[3][3], rhs[3], v[3];
+                /* (1 + H) v = j/n + g/2 + C_prev/(2n) + H v_prev, H = kappa beta t_prev / 6 */
+                double H = h * s->Tprev[i] / 3.0;
                 for (int a = 0; a < 3; a++) {
                     s->j[a * N + i] = j[a];
-                    rhs[a] = (j[a] + 0.5 * (n * s->g[a] + s->Cprev[a * N + i])) / n;
-                    for (int b = 0; b < 3; b++) {
-                        M[a][b] = (a == b ? 1.0 : 0.0) + H[a][b];
-                        rhs[a] += H[a][b] * s->vprev[b * N + i];
-                    }
+                    double rhs = (j[a] + 0.5 * (n * s->g[a] + s->Cprev[a * N + i])) / n + H * s->vprev[a * N + i];
+                    s->us[a * N + i] = rhs / (1.0 + H);
                 }
-                solve3(M, rhs, v);
-                for (int d = 0; d < 3; d++) s->us[d * N + i] = v[d];
             }
 }
 
@@ -351,7 +327,7 @@ static void smeared_density(wo_state *s)
 
 /* Step 2 of Sec. 5: the fields C (Eq. campoc, split as n (F^mf + F^viscous))
  * and A (Eq. campod) as sums over the contact shell (R2, R4), with
- * du = v(r+e) - v(r) (R7), plus the tensor T of R7 for the next step. */
+ * du = v(r+e) - v(r) (R7), plus t of R7 for the next step. */
 static void shell_fields(wo_state *s)
 {
     long N = s->N;
@@ -360,7 +336,7 @@ static void shell_fields(wo_state *s)
     double chi_of_n = M_PI * s->sigma * s->sigma * s->sigma / 6.0;
     memset(s->Cf, 0, sizeof(double) * 3 * N);
     memset(s->A, 0, sizeof(double) * 6 * N);
-    memset(s->Tcur, 0, sizeof(double) * 6 * N);
+    memset(s->Tcur, 0, sizeof(double) * N);
     if (!s->interactions) return;
     for (int z = 0; z < s->nz; z++)
         for (int y = 0; y < s->ny; y++)
@@ -368,7 +344,7 @@ static void shell_fields(wo_state *s)
                 if (is_wall(s, z)) continue;
                 long i = x + (long)s->nx * (y + (long)s->ny * z);
                 double ni = s->n[i];
-                double Fmf[3] = {0, 0, 0}, Fv[3] = {0, 0, 0}, S[3][3] = {{0}}, T[3][3] = {{0}};
+                double Fmf[3] = {0, 0, 0}, Fv[3] = {0, 0, 0}, S[3][3] = {{0}}, t = 0.0;
                 for (int m = 0; m < s->nshell; m++) {
                     int ex = s->shell[3 * m], ey = s->shell[3 * m + 1], ez = s->shell[3 * m + 2];
                     long k = neighbour(s, x, y, z, ex, ey, ez);
@@ -384,11 +360,9 @@ static void shell_fields(wo_state *s)
                     for (int a = 0; a < 3; a++) {
                         Fmf[a] += -CS2 * sig2 * wgn * kh[a];
                         Fv[a] += beta * wgn * kh[a] * kdu;
-                        for (int b = 0; b < 3; b++) {
-                            S[a][b] += wgn * (kh[b] * du[a] + kh[a] * du[b]);
-                            T[a][b] += wgn * kh[a] * kh[b];
-                        }
+                        for (int b = 0; b < 3; b++) S[a][b] += wgn * (kh[b] * du[a] + kh[a] * du[b]);
                     }
+                    t += wgn;
                 }
                 for (int d = 0; d < 3; d++) s->Cf[d * N + i] = ni * (Fmf[d] + Fv[d]);
                 double pa = -(CS2 / 5.0) * ni * sig2;
@@ -398,8 +372,7 @@ static void shell_fields(wo_state *s)
                 s->A[3 * N + i] = pa * S[0][1];
                 s->A[4 * N + i] = pa * S[0][2];
                 s->A[5 * N + i] = pa * S[1][2];
-                s->Tcur[0 * N + i] = T[0][0]; s->Tcur[1 * N + i] = T[1][1]; s->Tcur[2 * N + i] = T[2][2];
-                s->Tcur[3 * N + i] = T[0][1]; s->Tcur[4 * N + i] = T[0][2]; s->Tcur[5 * N + i] = T[1][2];
+                s->Tcur[i] = t;
             }
 }
 
@@ -499,7 +472,7 @@ int wo_step(wo_state *s, long nsteps)
         shell_fields(s);
         collide_stream(s);
         memcpy(s->Cprev, s->Cf, sizeof(double) * 3 * N);
-        memcpy(s->Tprev, s->Tcur, sizeof(double) * 6 * N);
+        memcpy(s->Tprev, s->Tcur, sizeof(double) * N);
         memcpy(s->vprev, s->us, sizeof(double) * 3 * N);
         s->steps++;
     }
