@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the WDLB lattice update on GB300.
+
+Workload: bulk periodic box 128^3, sigma = 4 lattice units, packing fraction
+0.3, FP32 deviation storage with FP64 reductions, transverse shear wave
+u_x = 1e-4 sin(2 pi z / 128) on a uniform density with seeded 1e-4 relative
+noise.  One benchmark step = 100 lattice time steps (each: moments and field
+velocity, smeared density, shell sums + collision + streaming) followed by the
+FP64 pore-average reduction.  Metric: MLUPS (lattice-node updates per second).
+
+  python bench.py [--gpus N --steps K --warmup W]      this library (C ABI)
+  python bench.py --impl reference ...                 the FP64 CPU oracle
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own replica of the
+box (the workload has no exchange step): weak scaling, no collective on the
+data path; the elapsed time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (lattice-node updates/s) & HBM roofline frac, batched FP32 vs plain FP64; p50/p99 solve"
+UNIT = "MLUPS"
+L = 128
+SIGMA = 4.0
+SUB = 100                      # lattice time steps per benchmark step
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+WORKLOAD = ("bulk periodic box 128^3, sigma=4 lattice units, packing fraction 0.3, D3Q19, "
+            "Carnahan-Starling contact value, K=2, tau=1, shear wave u_x=1e-4 sin(2 pi z/128), 1e-4 density noise")
+
+
+def shell_size(sigma):
+    R = int(math.floor(sigma + 0.5))
+    c = 0
+    for x in range(-R, R + 1):
+        for y in range(-R, R + 1):
+            for z in range(-R, R + 1):
+                r2 = x * x + y * y + z * z
+                if (sigma - 0.5) ** 2 < r2 <= (sigma + 0.5) ** 2:
+                    c += 1
+    return c
+
+
+# Algorithmic FP32 operations per node update of the shell + collide kernel
+# (an FMA counts 2): per shell vector 52 (contact value 9, velocity
+# difference 3, khat.dv and q khat.dv 6, the F^mf, F^viscous and A sums 36,
+# t 1), plus 475 for moments, collision and the force terms.
+FLOPS_PER_PAIR = 52
+FLOPS_COLLIDE = 475
+# Algorithmic HBM bytes per node update: read and write 19 populations.
+BYTES_PER_NODE = {"f64": 19 * 2 * 8, "f32": 19 * 2 * 4, "f16": 19 * 2 * 2}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1304_7880_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the shell kernel from a committed ncu summary,
+    used only if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "shell_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        if rec.get("source_hash") == kernel_source_hash() and rec.get("nodes") == L ** 3:
+            return rec.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_oracle(timesteps=1, box=L):
+    """The FP64 oracle on the host, as it stands (single thread)."""
+    import oracle
+    from paper_1304_7880_gb300 import synth
+    oracle.build()
+    p, n, u = synth.bulk_shear_128(L=box)
+    o = oracle.Oracle(p["nx"], p["ny"], p["nz"], p["walls"], p["sigma"], p["tau"], p["g"])
+    o.init(n, u)
+    t0 = time.perf_counter()
+    o.step(timesteps)
+    dt = time.perf_counter() - t0
+    nodes = box ** 3
+    return {"value": nodes * timesteps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d time step(s) of the %d^3 box (same sigma, density and initial fields), %.1f s"
+                      % (timesteps, box, dt)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    box = 32
+    per_step = 4
+    cfg = {"workload": WORKLOAD, "sample": "%d^3 box, %d time steps per benchmark step" % (box, per_step),
+           "nodes": box ** 3, "parallelism": "single host thread"}
+    import oracle
+    from paper_1304_7880_gb300 import synth
+    oracle.build()
+    p, n, u = synth.bulk_shear_128(L=box)
+    o = oracle.Oracle(p["nx"], p["ny"], p["nz"], p["walls"], p["sigma"], p["tau"], p["g"])
+    o.init(n, u)
+    for _ in range(args.warmup):
+        o.step(per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per_step)
+    dt = time.perf_counter() - t0
+    value = box ** 3 * per_step * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": cfg["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_1304_7880_gb300 import build, synth
+    if rank == 0:
+        build.build()
+    barrier()
+    from paper_1304_7880_gb300 import wdlb as w
+
+    p, n_h, u_h = synth.bulk_shear_128(seed=2 + rank)
+    N = L ** 3
+    shape = (p["nx"], p["ny"], p["nz"])
+
+    def make(storage):
+        ctx = w.wdlb_create(shape, p["sigma"], p["walls"], p["tau"], p["g"], storage=storage)
+        d_n = torch.from_numpy(n_h).cuda()
+        d_u = torch.from_numpy(u_h).cuda()
+        torch.cuda.synchronize()
+        w.wdlb_init_fields_device(ctx, d_n, d_u)
+        ctx.stream.synchronize()
+        return ctx
+
+    # ---------------- device-resident timed region (FP32 path) ----------------
+    ctx = make("f32")
+    for _ in range(args.warmup):
+        w.wdlb_profile_step(ctx, SUB)
+        w.wdlb_pore_average(ctx)
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    launches0 = w.wdlb_launch_count(ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(ctx.stream)
+    kms = [0.0, 0.0, 0.0]
+    for _ in range(args.steps):
+        ms = w.wdlb_profile_step(ctx, SUB)
+        for k in range(3):
+            kms[k] += ms[k] / args.steps
+        w.wdlb_pore_average(ctx)
+    ev1.record(ctx.stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if rank == 0 else None
+    gpu_launches = w.wdlb_launch_count(ctx) - launches0
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    value = world * N * SUB * args.steps / (elapsed_ms * 1e-3) / 1e6
+    stats = w.wdlb_pore_average(ctx)
+
+    # ---------------- end to end through host buffers ----------------
+    pin_n = torch.empty(n_h.shape, dtype=torch.float64, pin_memory=True)
+    pin_u = torch.empty(u_h.shape, dtype=torch.float64, pin_memory=True)
+    pin_n.copy_(torch.from_numpy(n_h))
+    pin_u.copy_(torch.from_numpy(u_h))
+    out_n = torch.empty(n_h.shape, dtype=torch.float64, pin_memory=True)
+    out_u = torch.empty(u_h.shape, dtype=torch.float64, pin_memory=True)
+    hn, hu, on, ou = pin_n.numpy(), pin_u.numpy(), out_n.numpy(), out_u.numpy()
+    e2e_steps = max(2, args.steps // 2)
+    for _ in range(1):
+        w.wdlb_init_fields(ctx, hn, hu)
+        w.wdlb_step(ctx, SUB)
+        w.wdlb_moments(ctx, on, ou)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        w.wdlb_init_fields(ctx, hn, hu)
+        w.wdlb_step(ctx, SUB)
+        w.wdlb_moments(ctx, on, ou)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    e2e_value = world * N * SUB * e2e_steps / e2e_s / 1e6
+    assert np.isfinite(on).all()
+
+    # ---------------- other storage paths (same workload, shorter) ----------------
+    paths = {}
+    for storage, sub, reps in (("f64", 10, 2), ("f16", SUB, 3)):
+        c2 = make(storage)
+        w.wdlb_profile_step(c2, sub)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(c2.stream)
+        pk = [0.0, 0.0, 0.0]
+        for _ in range(reps):
+            ms = w.wdlb_profile_step(c2, sub)
+            for k in range(3):
+                pk[k] += ms[k] / reps
+        b.record(c2.stream)
+        torch.cuda.synchronize()
+        t = max_over_ranks(a.elapsed_time(b))
+        mlups = world * N * sub * reps / (t * 1e-3) / 1e6
+        paths[storage] = {"value": mlups, "unit": UNIT, "kernels_ms": pk,
+                          "hbm_frac_of_measured": mlups * 1e6 * BYTES_PER_NODE[storage] / 1e9
+                          / measured_peaks()[0]["hbm_gbs"]}
+        w.wdlb_destroy(c2)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---------------- roofline of the dominant kernel ----------------
+    peaks, peak_kind = measured_peaks()
+    nshell = shell_size(SIGMA)
+    flops_per_node = nshell * FLOPS_PER_PAIR + FLOPS_COLLIDE
+    shell_ms = kms[2]
+    achieved_tflops = flops_per_node * N / (shell_ms * 1e-3) / 1e12
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    step_ms = sum(kms)
+    hbm_achieved = BYTES_PER_NODE["f32"] * N / (step_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_shell_collide", "achieved": achieved_tflops, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak, "traffic": recorded_traffic(),
+                "peak_source": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts)",
+                "flops_per_node": flops_per_node,
+                "share_of_step": shell_ms / step_ms if step_ms > 0 else None,
+                "hbm": {"achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
+                        "bytes_per_node": BYTES_PER_NODE["f32"]}}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": N, "time_steps_per_step": SUB,
+                       "storage": "f32 deviation from w_q n_ref, FP64 reductions",
+                       "l2": "no flush: populations 2 x 159 MB + fields exceed the 129 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hn.nbytes + hu.nbytes),
+                    "d2h_bytes_per_step": int(on.nbytes + ou.nbytes),
+                    "path": "wdlb_init_fields(host) + wdlb_step(100) + wdlb_moments(host), pinned buffers"},
+            "clocks": clocks, "gpu_launches": int(gpu_launches),
+            "kernels_ms": {"moments": kms[0], "smeared_density": kms[1], "shell_collide_stream": kms[2]},
+            "paths": paths, "pore_average": {k: stats[k] for k in ("mass", "mean_n", "mean_ux", "steps")}}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

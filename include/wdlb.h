@@ -1,0 +1,202 @@
+/*
+ * wdlb.h - C ABI of the GB300 Weighted Density Lattice Boltzmann (WDLB)
+ * library: the per-timestep lattice update of Marini Bettolo Marconi &
+ * Melchionna, "Weighted density Lattice Boltzmann approach to fluids under
+ * confinement" (arXiv:1304.7880), run as sm_103a CUDA kernels.
+ *
+ * One call of wdlb_step advances the five-step algorithm of Sec. 5 (Numerical
+ * results) by one or more time steps on one lattice ("pore"):
+ *   fields   smeared density nbar (Sec. 3, Fischer-Methfessel prescription),
+ *            C = n (F^mf + F^viscous) (Sec. 3, Eq. campoc) and the SMDB field
+ *            A (Eq. campod), as sums over the contact shell |e| ~ sigma;
+ *   collide  BGK relaxation (Eq. relaxationtime) plus the hydrodynamic
+ *            projection with force n g + C and the A-term (Eq. SMDB,
+ *            Eq. eq:dufty2), second-order (trapezoidal) in time;
+ *   stream   D3Q19 (Sec. 5), periodic in x and y (and z without walls),
+ *            half-way bounce-back on the smooth walls z = 0 and z = nz-1.
+ *
+ * Units: lattice units, spacing = time step = mass = 1, k_B T = 1/3.
+ * Layout of every per-node array exchanged through this header: node index
+ * i = x + nx*(y + ny*z); vector fields are three consecutive arrays of N
+ * values (x components, then y, then z), N = nx*ny*nz.
+ *
+ * Threading: a context may be used by one host thread at a time.  All device
+ * work of a context is issued on its stream (wdlb_options.stream); calls that
+ * return host data synchronise that stream.
+ *
+ * Errors: every call returns a wdlb_status; wdlb_last_error(ctx) gives a
+ * message.  No call aborts the process.  A kernel that detects a non-physical
+ * state (packing fraction of the smeared density >= 1, non-finite or
+ * non-positive density) records it in a device status word; the next call
+ * that synchronises returns WDLB_ERR_UNSTABLE.
+ */
+#ifndef WDLB_H
+#define WDLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wdlb_ctx wdlb_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    WDLB_OK = 0,
+    WDLB_ERR_ARG = 1,      /* invalid argument; nothing was changed             */
+    WDLB_ERR_OOM = 2,      /* device allocation failed or workspace too small   */
+    WDLB_ERR_CUDA = 3,     /* a CUDA call failed; message in wdlb_last_error    */
+    WDLB_ERR_UNSTABLE = 4, /* smeared packing fraction >= 1 or non-finite state */
+    WDLB_ERR_TIMEOUT = 5,  /* a bounded device wait ran out                     */
+    WDLB_ERR_STATE = 6     /* call out of order (e.g. step before init)         */
+} wdlb_status;
+
+typedef struct {
+    int32_t nx, ny, nz;
+} wdlb_lattice;
+
+enum { WDLB_WALLS_NONE = 0, WDLB_WALLS_Z = 1 };
+/* Contact value g2(sigma+) of the homogeneous hard-sphere fluid at packing
+ * fraction chi = pi n sigma^3 / 6 (Sec. 3 leaves it open):
+ * Carnahan-Starling (1 - chi/2)/(1 - chi)^3, Percus-Yevick (1 + chi/2)/(1 - chi)^2,
+ * or 1 (test closure). */
+enum { WDLB_CLOSURE_CS = 0, WDLB_CLOSURE_PY = 1, WDLB_CLOSURE_ONE = 2 };
+/* Relaxation frequency: constant 1/tau, or (Sec. 4, omega0 proportional to
+ * n g2) tau(r) - 1/2 = (tau - 1/2) n_ref g2(n_ref) / (nbar(r) g2(nbar(r))),
+ * clamped to tau >= 0.501. */
+enum { WDLB_OMEGA_CONST = 0, WDLB_OMEGA_NBAR = 1 };
+/* Population storage: plain FP64 (FP64 arithmetic), FP32 deviation from the
+ * rest state w_q n_ref (FP32 arithmetic), FP16 relative deviation
+ * f_q / (w_q n_ref) - 1 (FP32 arithmetic). */
+enum { WDLB_STORE_F64 = 0, WDLB_STORE_F32 = 1, WDLB_STORE_F16 = 2 };
+
+typedef struct {
+    int32_t closure;          /* WDLB_CLOSURE_*, default CS                          */
+    int32_t omega_mode;       /* WDLB_OMEGA_*, default CONST                         */
+    int32_t storage;          /* WDLB_STORE_*, default F32                           */
+    int32_t interactions;     /* 1: fields C and A on (default); 0: plain BGK + g    */
+    double k_cross;           /* K: the A-term carries K * traceless(A) in its second
+                                 moment; 2 reproduces Eq. extrapressure (default)    */
+    double n_ref;             /* reference density (storage offset, NBAR mode);
+                                 0: mean fluid density of the initial state          */
+    void *workspace;          /* caller-owned device buffer of at least
+                                 wdlb_workspace_size bytes, 256-byte aligned, valid
+                                 until wdlb_destroy; NULL: the library allocates     */
+    uint64_t workspace_bytes; /* size of workspace                                   */
+    void *stream;             /* cudaStream_t for all work; NULL: the library creates
+                                 (and destroys) its own non-blocking stream          */
+} wdlb_options;
+
+/* Fill *opt with the defaults above.  opt must not be NULL. */
+void wdlb_default_options(wdlb_options *opt);
+
+/* Device bytes the context needs for this lattice and options (populations
+ * double-buffered, field arrays, staging and reduction scratch).  No GPU call. */
+wdlb_status wdlb_workspace_size(wdlb_lattice lat, double sigma, int32_t walls,
+                                const wdlb_options *opt, uint64_t *bytes);
+
+/* Create a context for one lattice (Sec. 5: cubic lattice, D3Q19).
+ *   lat    nx, ny >= 1; nz >= 3 with walls, >= 1 without; N < 2^31.
+ *   sigma  hard-sphere diameter in lattice units, 1 <= sigma <= 8.
+ *   walls  WDLB_WALLS_NONE (periodic box) or WDLB_WALLS_Z (slit: solid planes
+ *          z = 0 and z = nz-1, fluid in between; hydrodynamic width nz - 2).
+ *   tau    BGK relaxation time, tau > 0.5 (omega0 = 1/tau of Eq. relaxationtime).
+ *   g      external acceleration F/m of Eq. uno (3 doubles, host memory).
+ *   opt    options or NULL for defaults.
+ * On success *out owns the device memory (or uses opt->workspace).  The state
+ * is undefined until wdlb_init_fields. */
+wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double tau,
+                        const double g[3], const wdlb_options *opt, wdlb_ctx **out);
+
+/* Step 1 of the algorithm of Sec. 5: populations set to the discrete local
+ * equilibrium of density n and velocity u (host arrays of N and 3N doubles;
+ * u may be NULL for rest).  Density at solid nodes is ignored.  Synchronous. */
+wdlb_status wdlb_init_fields(wdlb_ctx *ctx, const double *n, const double *u);
+
+/* Same with device arrays (d_n: N doubles, d_u: 3N doubles or NULL), enqueued
+ * on the context stream. */
+wdlb_status wdlb_init_fields_device(wdlb_ctx *ctx, const double *d_n, const double *d_u);
+
+/* Steps 2-5 of the algorithm of Sec. 5, nsteps >= 0 times.  Asynchronous on
+ * the context stream (captured in a CUDA graph for repeated step counts). */
+wdlb_status wdlb_step(wdlb_ctx *ctx, int64_t nsteps);
+
+/* Step 4 of Sec. 5 / Eq. colonna: density n (N doubles) and field velocity v
+ * (3N doubles) of the current populations into host arrays (either may be
+ * NULL).  v is the velocity the next step's fields use: the lagged
+ * linear-implicit predictor of the second-order velocity u = (j + F/2)/n,
+ *   (1 + H) v = j/n + g/2 + C_prev/(2n) + H v_prev,
+ *   H = (kappa beta / 6) t_prev,  t = sum_e w g2 n(r+e),  kappa = 2,
+ *   beta = 2 sigma^2 sqrt(kT/pi),
+ * equal to u at a steady state.  Solid nodes report 0.  Synchronous. */
+wdlb_status wdlb_moments(wdlb_ctx *ctx, double *n, double *u);
+
+/* Same into device arrays, enqueued on the context stream. */
+wdlb_status wdlb_moments_device(wdlb_ctx *ctx, double *d_n, double *d_u);
+
+/* Intermediate fields of the current state (step 2 of Sec. 5), host arrays,
+ * any may be NULL: nbar (N), C (3N, Eq. campoc), A (6N: xx, yy, zz, xy, xz, yz,
+ * Eq. campod, before removing its trace), u (3N, the collision velocity
+ * (j + F/2)/n with F = n g + C).  Does not advance the state.  Synchronous;
+ * allocates temporary device memory for its FP64 outputs. */
+wdlb_status wdlb_fields(wdlb_ctx *ctx, double *nbar, double *C, double *A, double *u);
+
+/* Populations f_q of the current state as FP64 (19N doubles, q-major, in the
+ * order of wdlb_velocity_set), solid nodes 0.  Synchronous. */
+wdlb_status wdlb_get_populations(wdlb_ctx *ctx, double *f);
+
+/* Pore-averaged quantities (abstract: pore-averaged properties), reduced in
+ * FP64 on the device over fluid nodes: mean density, mean u_x, flux
+ * sum(n u_x)/(nx ny), mass sum(n), eta_eff = <n> g_x H^2 / (12 <u_x>) with
+ * H = nz - 2 (NaN without walls), the last steady-state residual (NaN if none)
+ * and the step count.  Synchronous. */
+typedef struct {
+    double mean_n, mean_ux, flux_x, mass, eta_eff, residual;
+    int64_t steps;
+} wdlb_pore_stats;
+wdlb_status wdlb_pore_average(wdlb_ctx *ctx, wdlb_pore_stats *out);
+
+/* Steady-state driver: step in blocks of check_every (>= 1) steps; after each
+ * block compute in FP64 r = max|u_x(t) - u_x(t - check_every)| /
+ * (check_every * max|u_x(t)|) and stop when r < tol or after max_steps.
+ * *steps_done and *residual (either may be NULL) report the outcome. */
+wdlb_status wdlb_run_steady(wdlb_ctx *ctx, double tol, int32_t check_every, int64_t max_steps,
+                            int64_t *steps_done, double *residual);
+
+/* Library tables, host only, no GPU needed.
+ * wdlb_velocity_set: the 19 D3Q19 velocities (c: 57 int32, q-major) and
+ * weights (w: 19 doubles) in the library's population order.
+ * wdlb_stencil: which = 0 the smeared-density ball {b : |b|^2 <= (sigma/2)^2},
+ * which = 1 the contact shell {e : (sigma-1/2)^2 < |e|^2 <= (sigma+1/2)^2};
+ * writes up to cap vectors (3 int32 each) into vecs (may be NULL), the full
+ * count into *count, and for the shell the uniform quadrature weight w with
+ * sigma^2 sum_e w (e_z^2/|e|) = 4 pi sigma^3 / 3 into *weight (may be NULL). */
+wdlb_status wdlb_velocity_set(int32_t *c, double *w);
+wdlb_status wdlb_stencil(double sigma, int32_t which, int32_t *vecs, int32_t cap,
+                         int32_t *count, double *weight);
+
+/* Advance nsteps (>= 1) like wdlb_step, but launch the three kernels of each
+ * step one by one with CUDA events around each on the context stream, and
+ * write the mean device time per launch in milliseconds: ms[0] moments and
+ * field velocity, ms[1] smeared density, ms[2] shell sums + collision +
+ * streaming.  Synchronous. */
+wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3]);
+
+/* Number of kernels this context has launched so far (a graph replay counts
+ * the kernels it contains). */
+int64_t wdlb_launch_count(const wdlb_ctx *ctx);
+
+/* Human-readable message of the last error of ctx ("" if none; ctx may be NULL
+ * for errors of wdlb_create). */
+const char *wdlb_last_error(const wdlb_ctx *ctx);
+
+/* Release the context and its device memory (not a caller workspace).
+ * NULL-safe.  Synchronises the context stream first. */
+void wdlb_destroy(wdlb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WDLB_H */

@@ -1,0 +1,124 @@
+// Shared definitions of the WDLB CUDA library (device and host side).
+//
+// Lattice: D3Q19 (Sec. 5, Numerical results), lattice units with k_B T = 1/3.
+// This library's population order: rest; faces +x -x +y -y +z -z; edges
+// (+x+y) (-x-y) (+x-y) (-x+y) (+x+z) (-x-z) (+x-z) (-x+z) (+y+z) (-y-z)
+// (+y-z) (-y+z).  Opposite directions are adjacent (q, q^1 for q >= 1).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wdlb {
+
+constexpr int NQ = 19;
+constexpr double CS2 = 1.0 / 3.0;
+constexpr double KAPPA = 2.0;   // implicit factor of the field-velocity predictor
+
+__host__ __device__ constexpr int cx_of(int q)
+{
+    constexpr int t[NQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[q];
+}
+__host__ __device__ constexpr int cy_of(int q)
+{
+    constexpr int t[NQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[q];
+}
+__host__ __device__ constexpr int cz_of(int q)
+{
+    constexpr int t[NQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[q];
+}
+__host__ __device__ constexpr double w_of(int q)
+{
+    return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+__host__ __device__ constexpr int opp_of(int q) { return q == 0 ? 0 : (((q - 1) ^ 1) + 1); }
+
+template <class T>
+struct alignas(4 * sizeof(T)) V4 {
+    T x, y, z, w;
+};
+
+// Scalar parameters of one lattice, passed by value to every kernel.
+struct KParams {
+    int nx, ny, nz, walls;   // walls: solid planes z = 0 and z = nz-1
+    int N, Npad;             // node count, padded stride of per-node arrays
+    int nshell, nball;
+    int closure, omega_mode, interactions;
+    double g[3];             // external acceleration
+    double omega;            // 1/tau
+    double tau;
+    double k_cross;          // K of the A-term
+    double n_off;            // storage offset density (0 for FP64)
+    double inv_n_off;        // 1/n_off (FP16 scaling), 1 if n_off == 0
+    double sig2;             // sigma^2
+    double beta;             // 2 sigma^2 sqrt(kT/pi)
+    double wshell;           // uniform shell weight
+    double chi_of_n;         // pi sigma^3 / 6
+    double c_half;           // chi_of_n / (2 |ball|): half packing fraction per ball sum
+    double ref_ng;           // n_ref g2(n_ref) (NBAR mode)
+    double h_pred;           // kappa beta / 6: implicit factor of the field-velocity predictor per unit t
+};
+
+// Device buffers of one lattice.  S: storage type of populations; T: compute type.
+template <class S, class T>
+struct KBufs {
+    const S *f_in;
+    S *f_out;
+    V4<T> *nu;           // (n, v_x, v_y, v_z) per node: density and field velocity
+    T *hb;               // half smeared packing fraction per node
+    T *cprev;            // C of the previous step, 3 x Npad
+    T *tprev;            // t = sum_e w g2 n(r+e) of the previous step
+    const int4 *shell_e; // shell vectors
+    const V4<T> *shell_k;// unit vectors e/|e|
+    const int4 *ball;    // ball vectors
+    int *status;         // [0]: unstable flag
+    double *out_nbar, *out_C, *out_A, *out_u;   // field outputs (fields kernel only)
+};
+
+// Contact value of the homogeneous hard-sphere pair distribution at packing
+// fraction chi (closure 0: Carnahan-Starling, 1: Percus-Yevick, 2: one).
+template <int CL, class T>
+__device__ __forceinline__ T contact_g(T chi)
+{
+    if (CL == 2) return T(1);
+    T s = T(1) - chi;
+    if (CL == 0) return (T(0.5) + T(0.5) * s) / (s * s * s);
+    return (T(1.5) - T(0.5) * s) / (s * s);
+}
+
+inline double contact_g_host(int closure, double chi)
+{
+    if (closure == 2) return 1.0;
+    double s = 1.0 - chi;
+    if (closure == 0) return (0.5 + 0.5 * s) / (s * s * s);
+    return (1.5 - 0.5 * s) / (s * s);
+}
+
+// Population storage.  FP64: f itself.  FP32: f - w_q n_off.  FP16:
+// (f - w_q n_off) / (w_q n_off), the relative deviation from the rest state.
+template <class S>
+struct Store;
+template <>
+struct Store<double> {
+    typedef double T;
+    __device__ __forceinline__ static double load(const double *p, double) { return *p; }
+    __device__ __forceinline__ static void put(double *p, double v, double) { *p = v; }
+};
+template <>
+struct Store<float> {
+    typedef float T;
+    __device__ __forceinline__ static float load(const float *p, float) { return *p; }
+    __device__ __forceinline__ static void put(float *p, float v, float) { *p = v; }
+};
+template <>
+struct Store<__half> {
+    typedef float T;
+    __device__ __forceinline__ static float load(const __half *p, float scale) { return __half2float(*p) * scale; }
+    __device__ __forceinline__ static void put(__half *p, float v, float inv_scale) { *p = __float2half_rn(v * inv_scale); }
+};
+
+}  // namespace wdlb

@@ -1,0 +1,62 @@
+// Host-side launchers of the WDLB kernels, one set per population storage
+// (compiled from wdlb_launch.cu once per storage type).  Every launcher
+// enqueues on `st`, adds the number of kernels it launched to *launches and
+// returns the first CUDA error.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wdlb_common.cuh"
+
+namespace wdlb {
+
+// Untyped device buffers of one lattice; the launcher casts them to its storage.
+struct DevBufs {
+    void *f[2];          // populations, double buffer
+    void *nu;            // V4<T> per node
+    void *hb;            // T per node
+    void *cprev;         // 3 x Npad T
+    void *tprev;         // Npad T
+    const int4 *shell_e;
+    const void *shell_k; // V4<T> per shell vector
+    const int4 *ball;
+    int *status;
+    double *stage;       // >= 4 N doubles (FP64 staging of n and u)
+    double *snap;        // N doubles (u_x snapshot)
+    double *partial;     // >= kStatBlocks * 6 doubles
+    double *result;      // >= 8 doubles
+};
+
+constexpr int kStatBlocks = 304;
+
+struct Launchers {
+    cudaError_t (*init)(const KParams &, const DevBufs &, int cur, const double *d_n, const double *d_u,
+                        cudaStream_t, int64_t *launches);
+    // one time step from buffer `cur` into `cur ^ 1`
+    cudaError_t (*step)(const KParams &, const DevBufs &, int cur, cudaStream_t, int64_t *launches);
+    // one kernel of a time step from buffer `cur`: part 0 moments, 1 ball, 2 shell + collide + stream
+    cudaError_t (*step_part)(const KParams &, const DevBufs &, int cur, int part, cudaStream_t, int64_t *launches);
+    // fields of the state in buffer `cur` (moments, ball and the shell sums; no streaming)
+    cudaError_t (*fields)(const KParams &, const DevBufs &, int cur, double *nbar, double *C, double *A,
+                          double *u, cudaStream_t, int64_t *launches);
+    // moments of the state in buffer `cur` into FP64 device arrays (either may be NULL)
+    cudaError_t (*moments)(const KParams &, const DevBufs &, int cur, double *d_n, double *d_u, cudaStream_t,
+                           int64_t *launches);
+    // population q of buffer `cur` as FP64 into out (N doubles)
+    cudaError_t (*population)(const KParams &, const DevBufs &, int cur, int q, double *out, cudaStream_t,
+                              int64_t *launches);
+    // moments of buffer `cur`, then FP64 statistics into result[0..5] (see k_stats)
+    cudaError_t (*stats)(const KParams &, const DevBufs &, int cur, int update_snap, cudaStream_t,
+                         int64_t *launches);
+};
+
+const Launchers &launchers_f64();
+const Launchers &launchers_f32();
+const Launchers &launchers_f16();
+
+// FP64 sum of d_n over fluid nodes into *result (device), one launch pair.
+cudaError_t launch_sum_density(const KParams &, const double *d_n, double *partial, double *result,
+                               cudaStream_t, int64_t *launches);
+
+}  // namespace wdlb

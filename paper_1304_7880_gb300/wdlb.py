@@ -1,0 +1,265 @@
+"""ctypes binding of the WDLB C ABI (``include/wdlb.h``), same names.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``libwdlb.so``.  PyTorch supplies the device memory (one workspace tensor per
+context, handed to the library) and the CUDA stream.  There is no CPU path: if
+the compiled library is missing, loading fails with an error.
+
+Arrays: node index i = x + nx*(y + ny*z), numpy shape (nz, ny, nx); vectors
+(3, nz, ny, nx); A (6, nz, ny, nx) in the order xx, yy, zz, xy, xz, yz.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwdlb.so")
+_lib = None
+
+WDLB_OK = 0
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_UNSTABLE", 5: "ERR_TIMEOUT",
+                6: "ERR_STATE"}
+CLOSURES = {"CS": 0, "PY": 1, "ONE": 2}
+OMEGA_MODES = {"const": 0, "nbar": 1}
+STORAGES = {"f64": 0, "f32": 1, "f16": 2}
+
+
+class WDLBError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+class wdlb_lattice(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class wdlb_options(ctypes.Structure):
+    _fields_ = [("closure", ctypes.c_int32), ("omega_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("interactions", ctypes.c_int32), ("k_cross", ctypes.c_double), ("n_ref", ctypes.c_double),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p)]
+
+
+class wdlb_pore_stats(ctypes.Structure):
+    _fields_ = [("mean_n", ctypes.c_double), ("mean_ux", ctypes.c_double), ("flux_x", ctypes.c_double),
+                ("mass", ctypes.c_double), ("eta_eff", ctypes.c_double), ("residual", ctypes.c_double),
+                ("steps", ctypes.c_int64)]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libwdlb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libwdlb.so not built (%s); run paper_1304_7880_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "wdlb_default_options": (None, [P]),
+        "wdlb_workspace_size": (I32, [wdlb_lattice, D, I32, P, P]),
+        "wdlb_create": (I32, [wdlb_lattice, D, I32, D, P, P, P]),
+        "wdlb_init_fields": (I32, [P, P, P]),
+        "wdlb_init_fields_device": (I32, [P, P, P]),
+        "wdlb_step": (I32, [P, I64]),
+        "wdlb_moments": (I32, [P, P, P]),
+        "wdlb_moments_device": (I32, [P, P, P]),
+        "wdlb_fields": (I32, [P, P, P, P, P]),
+        "wdlb_get_populations": (I32, [P, P]),
+        "wdlb_pore_average": (I32, [P, P]),
+        "wdlb_run_steady": (I32, [P, D, I32, I64, P, P]),
+        "wdlb_velocity_set": (I32, [P, P]),
+        "wdlb_stencil": (I32, [D, I32, P, I32, P, P]),
+        "wdlb_profile_step": (I32, [P, I64, P]),
+        "wdlb_launch_count": (I64, [P]),
+        "wdlb_last_error": (ctypes.c_char_p, [P]),
+        "wdlb_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, ctx=None):
+    if status != WDLB_OK:
+        lib = load_library()
+        msg = lib.wdlb_last_error(ctx.handle if ctx is not None else None)
+        raise WDLBError(status, msg.decode() if msg else "")
+
+
+def _f64(a, shape) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != int(np.prod(shape)):
+        raise ValueError("expected %d values, got %d" % (int(np.prod(shape)), a.size))
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """Handle of one lattice plus the torch objects that back it."""
+
+    def __init__(self, handle, shape, workspace, stream, walls, g):
+        self.handle = handle
+        self.shape = shape          # (nz, ny, nx)
+        self.N = int(np.prod(shape))
+        self.workspace = workspace  # torch uint8 tensor (device memory)
+        self.stream = stream        # torch.cuda.Stream
+        self.walls = walls
+        self.g = g
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            wdlb_destroy(self)
+
+
+def wdlb_create(lattice, sigma, walls, tau, g=(0.0, 0.0, 0.0), closure="CS", omega_mode="const",
+                storage="f32", interactions=True, k_cross=2.0, n_ref=0.0, device=None):
+    """Create a context; device memory and stream come from PyTorch."""
+    import torch
+
+    lib = load_library()
+    nx, ny, nz = (int(v) for v in lattice)
+    lat = wdlb_lattice(nx, ny, nz)
+    opt = wdlb_options()
+    lib.wdlb_default_options(ctypes.byref(opt))
+    opt.closure = CLOSURES[closure]
+    opt.omega_mode = OMEGA_MODES[omega_mode]
+    opt.storage = STORAGES[storage]
+    opt.interactions = 1 if interactions else 0
+    opt.k_cross = float(k_cross)
+    opt.n_ref = float(n_ref)
+    walls_i = 1 if walls else 0
+    nbytes = ctypes.c_uint64()
+    _check(lib.wdlb_workspace_size(lat, float(sigma), walls_i, ctypes.byref(opt), ctypes.byref(nbytes)))
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=dev)
+    base = workspace.data_ptr()
+    aligned = (base + 255) & ~255
+    stream = torch.cuda.Stream(device=dev)
+    opt.workspace = ctypes.c_void_p(aligned)
+    opt.workspace_bytes = int(nbytes.value)
+    opt.stream = ctypes.c_void_p(stream.cuda_stream)
+    gg = (ctypes.c_double * 3)(*[float(v) for v in g])
+    handle = ctypes.c_void_p()
+    with torch.cuda.device(dev):
+        _check(lib.wdlb_create(lat, float(sigma), walls_i, float(tau), gg, ctypes.byref(opt), ctypes.byref(handle)))
+    return Context(handle, (nz, ny, nx), workspace, stream, bool(walls), tuple(float(v) for v in g))
+
+
+def wdlb_init_fields(ctx: Context, n, u=None):
+    lib = load_library()
+    n = _f64(n, ctx.shape)
+    uu = None if u is None else _f64(u, (3,) + ctx.shape)
+    _check(lib.wdlb_init_fields(ctx.handle, _ptr(n), None if uu is None else _ptr(uu)), ctx)
+
+
+def wdlb_init_fields_device(ctx: Context, d_n, d_u=None):
+    """d_n, d_u: float64 CUDA tensors (N and 3N values), read on the context stream."""
+    lib = load_library()
+    _check(lib.wdlb_init_fields_device(ctx.handle, ctypes.c_void_p(d_n.data_ptr()),
+                                       None if d_u is None else ctypes.c_void_p(d_u.data_ptr())), ctx)
+
+
+def wdlb_step(ctx: Context, nsteps: int = 1):
+    _check(load_library().wdlb_step(ctx.handle, int(nsteps)), ctx)
+
+
+def wdlb_moments(ctx: Context, n_out=None, u_out=None):
+    """Density and field velocity as numpy arrays (host; synchronous)."""
+    lib = load_library()
+    n = np.empty(ctx.shape) if n_out is None else n_out
+    u = np.empty((3,) + ctx.shape) if u_out is None else u_out
+    _check(lib.wdlb_moments(ctx.handle, _ptr(n), _ptr(u)), ctx)
+    return n, u
+
+
+def wdlb_moments_device(ctx: Context, d_n, d_u):
+    lib = load_library()
+    _check(lib.wdlb_moments_device(ctx.handle, None if d_n is None else ctypes.c_void_p(d_n.data_ptr()),
+                                   None if d_u is None else ctypes.c_void_p(d_u.data_ptr())), ctx)
+
+
+def wdlb_fields(ctx: Context):
+    """nbar, C, A, u (trapezoidal velocity) of the current state (host arrays)."""
+    lib = load_library()
+    nbar = np.empty(ctx.shape)
+    C = np.empty((3,) + ctx.shape)
+    A = np.empty((6,) + ctx.shape)
+    u = np.empty((3,) + ctx.shape)
+    _check(lib.wdlb_fields(ctx.handle, _ptr(nbar), _ptr(C), _ptr(A), _ptr(u)), ctx)
+    return nbar, C, A, u
+
+
+def wdlb_get_populations(ctx: Context) -> np.ndarray:
+    lib = load_library()
+    f = np.empty((19,) + ctx.shape)
+    _check(lib.wdlb_get_populations(ctx.handle, _ptr(f)), ctx)
+    return f
+
+
+def wdlb_pore_average(ctx: Context) -> dict:
+    lib = load_library()
+    st = wdlb_pore_stats()
+    _check(lib.wdlb_pore_average(ctx.handle, ctypes.byref(st)), ctx)
+    return {k: getattr(st, k) for k, _ in wdlb_pore_stats._fields_}
+
+
+def wdlb_run_steady(ctx: Context, tol: float, check_every: int = 100, max_steps: int = 10 ** 7):
+    lib = load_library()
+    done = ctypes.c_int64()
+    res = ctypes.c_double()
+    _check(lib.wdlb_run_steady(ctx.handle, float(tol), int(check_every), int(max_steps), ctypes.byref(done),
+                               ctypes.byref(res)), ctx)
+    return done.value, res.value
+
+
+def wdlb_velocity_set():
+    lib = load_library()
+    c = np.zeros((19, 3), dtype=np.int32)
+    w = np.zeros(19)
+    _check(lib.wdlb_velocity_set(_ptr(c), _ptr(w)))
+    return c, w
+
+
+def wdlb_stencil(sigma: float, which: int):
+    """which = 0: smeared-density ball; 1: contact shell (vectors, weight)."""
+    lib = load_library()
+    cnt = ctypes.c_int32()
+    w = ctypes.c_double()
+    _check(lib.wdlb_stencil(float(sigma), int(which), None, 0, ctypes.byref(cnt), ctypes.byref(w)))
+    v = np.zeros((cnt.value, 3), dtype=np.int32)
+    _check(lib.wdlb_stencil(float(sigma), int(which), _ptr(v), cnt.value, ctypes.byref(cnt), ctypes.byref(w)))
+    return v, w.value
+
+
+def wdlb_profile_step(ctx: Context, nsteps: int):
+    """Advance nsteps with per-kernel CUDA events; mean ms per launch of
+    (moments, smeared density, shell + collide + stream)."""
+    ms = (ctypes.c_double * 3)()
+    _check(load_library().wdlb_profile_step(ctx.handle, int(nsteps), ms), ctx)
+    return tuple(ms)
+
+
+def wdlb_launch_count(ctx: Context) -> int:
+    return int(load_library().wdlb_launch_count(ctx.handle))
+
+
+def wdlb_last_error(ctx: Context = None) -> str:
+    msg = load_library().wdlb_last_error(None if ctx is None else ctx.handle)
+    return msg.decode() if msg else ""
+
+
+def wdlb_destroy(ctx: Context):
+    if ctx.handle:
+        load_library().wdlb_destroy(ctx.handle)
+        ctx.handle = None

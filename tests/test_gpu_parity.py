@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances (stated per storage):
+  FP64 storage and arithmetic: 1e-10 relative (summation order only).
+  FP32 deviation storage: max relative error 1e-5 on n; on u, 1e-5 of max|u|.
+  FP16 relative-deviation storage: 2e-3 relative on n, 2e-2 of max|u| (10-bit
+  mantissa on f/(w n_ref) - 1).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1304_7880_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": (1e-10, 1e-10), "f32": (1e-5, 1e-5), "f16": (2e-3, 2e-2)}
+
+
+@pytest.fixture(scope="module")
+def w():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1304_7880_gb300 import build, wdlb
+    build.build()
+    return wdlb
+
+
+def make_pair(w, oracle_mod, p, n, u, storage="f64", **opt):
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    ctx = w.wdlb_create((nx, ny, nz), p["sigma"], p["walls"], p["tau"], p["g"], storage=storage, **opt)
+    w.wdlb_init_fields(ctx, n, u)
+    o = oracle_mod.Oracle(nx, ny, nz, p["walls"], p["sigma"], p["tau"], p["g"],
+                          **{k: v for k, v in opt.items() if k in ("closure", "omega_mode", "k_cross", "n_ref",
+                                                                   "interactions")})
+    o.init(n, u)
+    return ctx, o
+
+
+def fluid_mask(shape, walls):
+    m = np.ones(shape, dtype=bool)
+    if walls:
+        m[0] = m[-1] = False
+    return m
+
+
+def compare(ctx, o, walls, storage, w):
+    n_g, u_g = w.wdlb_moments(ctx)
+    n_o, u_o = o.moments()
+    m = fluid_mask(n_o.shape, walls)
+    en = np.max(np.abs(n_g[m] - n_o[m]) / np.abs(n_o[m]))
+    umax = np.abs(u_o[:, m]).max()
+    eu = np.max(np.abs(u_g[:, m] - u_o[:, m])) / umax if umax > 0 else np.max(np.abs(u_g[:, m]))
+    tn, tu = TOL[storage]
+    assert en <= tn, "n: max rel err %.3e > %.1e" % (en, tn)
+    assert eu <= tu, "u: max err / max|u| %.3e > %.1e" % (eu, tu)
+    return en, eu
+
+
+def random_state(shape, sigma, nstar, amp, seed, walls):
+    nz, ny, nx = shape
+    n, u = synth.uniform_with_noise(nx, ny, nz, nstar / sigma ** 3, amp, seed, walls)
+    rng = np.random.default_rng(seed)
+    u = 1e-3 * rng.standard_normal(u.shape)
+    if walls:
+        u[:, 0] = u[:, -1] = 0
+    return n, u
+
+
+@pytest.mark.parametrize("case", ["bulk_s3", "slit_s4"])
+def test_fields_match_oracle(w, oracle_mod, case):
+    if case == "bulk_s3":
+        p = dict(nx=9, ny=8, nz=7, walls=False, sigma=3.0, tau=0.9, g=(1e-5, 0, 0))
+    else:
+        p = dict(nx=8, ny=8, nz=21, walls=True, sigma=4.0, tau=1.0, g=(1e-5, 0, 0))
+    n, u = random_state((p["nz"], p["ny"], p["nx"]), p["sigma"], 0.5, 5e-2, 3, p["walls"])
+    ctx, o = make_pair(w, oracle_mod, p, n, u, "f64")
+    for _ in range(2):
+        nb_g, C_g, A_g, _ = w.wdlb_fields(ctx)
+        nb_o, C_o, A_o = o.fields()
+        m = fluid_mask(nb_o.shape, p["walls"])
+        np.testing.assert_allclose(nb_g[m], nb_o[m], rtol=1e-12)
+        np.testing.assert_allclose(C_g[:, m], C_o[:, m], rtol=0, atol=1e-11 * np.abs(C_o).max())
+        np.testing.assert_allclose(A_g[:, m], A_o[:, m], rtol=0, atol=1e-11 * np.abs(A_o).max())
+        # after a few steps the predictor carries C_prev, t_prev, v_prev
+        w.wdlb_step(ctx, 3)
+        o.step(3)
+
+
+def test_slit_8x8x41_f64(w, oracle_mod):
+    p, n, u = synth.slit_8x8x41()
+    ctx, o = make_pair(w, oracle_mod, p, n, u, "f64")
+    for _ in range(2):
+        w.wdlb_step(ctx, 100)
+        o.step(100)
+        compare(ctx, o, True, "f64", w)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_slit_8x8x41_reduced_precision(w, oracle_mod, storage):
+    """The plain slit workload, 1000 steps, against the FP64 oracle."""
+    p, n, u = synth.slit_8x8x41()
+    ctx, o = make_pair(w, oracle_mod, p, n, u, storage)
+    for _ in range(10):
+        w.wdlb_step(ctx, 100)
+        o.step(100)
+    en, eu = compare(ctx, o, True, storage, w)
+    print("%s 8x8x41 1000 steps: n err %.2e, u err %.2e" % (storage, en, eu))
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_bulk_shear_wave_32(w, oracle_mod, storage):
+    p, n, u = synth.bulk_shear_128(L=32)
+    ctx, o = make_pair(w, oracle_mod, p, n, u, storage)
+    w.wdlb_step(ctx, 20)
+    o.step(20)
+    compare(ctx, o, False, storage, w)
+
+
+def test_bulk_shear_wave_128_full_size(w, oracle_mod):
+    """The bench workload (128^3, FP32, one launch configuration): two steps
+    against the oracle on every node; conservation of mass and momentum in FP64."""
+    p, n, u = synth.bulk_shear_128()
+    ctx, o = make_pair(w, oracle_mod, p, n, u, "f32")
+    w.wdlb_step(ctx, 2)
+    o.step(2)
+    compare(ctx, o, False, "f32", w)
+    st0 = w.wdlb_pore_average(ctx)
+    w.wdlb_step(ctx, 64)
+    st1 = w.wdlb_pore_average(ctx)
+    assert abs(st1["mass"] - st0["mass"]) / st0["mass"] < 1e-6
+
+
+EDGE_CASES = {
+    "column_slit": (dict(nx=1, ny=1, nz=40, walls=True, sigma=4.0, tau=1.0, g=(1e-5, 0, 0)), {}),
+    "ragged_periodic_s3": (dict(nx=13, ny=7, nz=19, walls=False, sigma=3.0, tau=0.8, g=(0, 1e-5, 0)), {}),
+    "tiny_slit_s1": (dict(nx=3, ny=2, nz=5, walls=True, sigma=1.0, tau=1.0, g=(1e-5, 0, 0)), {}),
+    "slit_s6": (dict(nx=10, ny=10, nz=30, walls=True, sigma=6.0, tau=1.0, g=(1e-5, 0, 0)), {}),
+    "nbar_mode": (dict(nx=8, ny=8, nz=21, walls=True, sigma=4.0, tau=1.0, g=(1e-5, 0, 0)),
+                  {"omega_mode": "nbar", "n_ref": 0.5 / 64}),
+    "py_closure": (dict(nx=8, ny=8, nz=16, walls=False, sigma=4.0, tau=1.0, g=(0, 0, 1e-5)), {"closure": "PY"}),
+    "one_closure_k0": (dict(nx=8, ny=8, nz=16, walls=False, sigma=4.0, tau=1.0, g=(0, 0, 0)),
+                       {"closure": "ONE", "k_cross": 0.0}),
+    "no_interactions": (dict(nx=5, ny=4, nz=21, walls=True, sigma=4.0, tau=0.7, g=(1e-5, 0, 0)),
+                        {"interactions": False}),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGE_CASES))
+def test_edge_cases_f64(w, oracle_mod, name):
+    p, opt = EDGE_CASES[name]
+    n, u = random_state((p["nz"], p["ny"], p["nx"]), p["sigma"], 0.4, 2e-2, 9, p["walls"])
+    ctx, o = make_pair(w, oracle_mod, p, n, u, "f64", **opt)
+    w.wdlb_step(ctx, 40)
+    o.step(40)
+    compare(ctx, o, p["walls"], "f64", w)
+    # populations agree too (matched by velocity vector)
+    f_g = w.wdlb_get_populations(ctx)
+    f_o = o.populations()
+    c_g, _ = w.wdlb_velocity_set()
+    c_o, _ = oracle_mod.velocities()
+    idx = [next(k for k in range(19) if (c_o[k] == c_g[q]).all()) for q in range(19)]
+    np.testing.assert_allclose(f_g, f_o[idx], rtol=0, atol=1e-12 * np.abs(f_o).max())
+
+
+def test_pore_average_matches_oracle(w, oracle_mod):
+    p, n, u = synth.slit_poiseuille(8, 8, 25, 0.3, 4.0, 1.0, 1e-6, seed=21)
+    ctx, o = make_pair(w, oracle_mod, p, n, u, "f64")
+    w.wdlb_step(ctx, 150)
+    o.step(150)
+    st = w.wdlb_pore_average(ctx)
+    n_o, u_o = o.moments()
+    ref = oracle_mod.pore_average(n_o, u_o, True, 1e-6)
+    for k in ("mean_n", "mean_ux", "flux_x", "eta_eff"):
+        assert st[k] == pytest.approx(ref[k], rel=1e-9), k
+    assert st["steps"] == 150
+
+
+def test_steady_state_poiseuille(w):
+    """Interactions off, tau at the bounce-back magic value: the steady profile
+    is the exact parabola, reached by the FP64 steady-state driver."""
+    tau = 0.5 + math.sqrt(3) / 4
+    nz, g = 21, 1e-6
+    ctx = w.wdlb_create((4, 4, nz), 4.0, True, tau, (g, 0, 0), storage="f64", interactions=False)
+    w.wdlb_init_fields(ctx, np.full((nz, 4, 4), 0.01))
+    steps, res = w.wdlb_run_steady(ctx, 1e-10, 100, 200000)
+    assert res < 1e-10 and steps < 200000
+    _, u = w.wdlb_moments(ctx)
+    nu = (tau - 0.5) / 3
+    z = np.arange(1, nz - 1)
+    np.testing.assert_allclose(u[0, 1:-1, 0, 0], g / (2 * nu) * (z - 0.5) * (nz - 1.5 - z), rtol=1e-7)
+    st = w.wdlb_pore_average(ctx)
+    assert st["eta_eff"] == pytest.approx(0.01 * nu, rel=1e-3)
+
+
+def test_graph_replay_equals_direct_launches(w):
+    p, n, u = synth.slit_8x8x41(seed=5)
+    a = w.wdlb_create((8, 8, 41), 4.0, True, 1.0, p["g"], storage="f32")
+    b = w.wdlb_create((8, 8, 41), 4.0, True, 1.0, p["g"], storage="f32")
+    w.wdlb_init_fields(a, n, u)
+    w.wdlb_init_fields(b, n, u)
+    w.wdlb_step(a, 96)                      # graph replays
+    for _ in range(96):
+        w.wdlb_step(b, 1)                   # direct launches
+    fa, fb = w.wdlb_get_populations(a), w.wdlb_get_populations(b)
+    assert np.array_equal(fa, fb)
+
+
+def test_device_and_host_entry_points_agree(w):
+    import torch
+    p, n, u = synth.slit_8x8x41(seed=6)
+    a = w.wdlb_create((8, 8, 41), 4.0, True, 1.0, p["g"], storage="f32")
+    w.wdlb_init_fields(a, n, u)
+    b = w.wdlb_create((8, 8, 41), 4.0, True, 1.0, p["g"], storage="f32")
+    dn = torch.from_numpy(n.copy()).cuda()
+    du = torch.from_numpy(u.copy()).cuda()
+    torch.cuda.synchronize()
+    w.wdlb_init_fields_device(b, dn, du)
+    w.wdlb_step(a, 10)
+    w.wdlb_step(b, 10)
+    on = torch.empty(dn.shape, dtype=torch.float64, device="cuda")
+    ou = torch.empty(du.shape, dtype=torch.float64, device="cuda")
+    w.wdlb_moments_device(b, on, ou)
+    b.stream.synchronize()
+    n_a, u_a = w.wdlb_moments(a)
+    assert np.array_equal(on.cpu().numpy(), n_a)
+    assert np.array_equal(ou.cpu().numpy(), u_a)
+
+
+def test_unstable_state_is_reported(w):
+    """A smeared packing fraction >= 1 is flagged by the kernels and reported
+    as WDLB_ERR_UNSTABLE at the next synchronising call."""
+    n = np.full((8, 8, 8), 2.5 / 64)   # n* = 2.5: chi = 1.31
+    ctx = w.wdlb_create((8, 8, 8), 4.0, False, 1.0, storage="f32")
+    w.wdlb_init_fields(ctx, n)
+    w.wdlb_step(ctx, 1)
+    with pytest.raises(w.WDLBError) as ei:
+        w.wdlb_moments(ctx)
+    assert ei.value.status == 4
+
+
+def test_step_before_init_is_rejected(w):
+    ctx = w.wdlb_create((4, 4, 4), 2.0, False, 1.0)
+    with pytest.raises(w.WDLBError) as ei:
+        w.wdlb_step(ctx, 1)
+    assert ei.value.status == 6
