@@ -276,6 +276,14 @@ def run_ours(args):
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
     value = world * N * SUB * args.steps / (elapsed_ms * 1e-3) / 1e6
     stats = w.wdlb_pore_average(ctx)
+    if args.only_device:
+        if rank == 0:
+            print(json.dumps({"only_device": True, "value": value, "unit": UNIT, "ms_per_step": elapsed_ms / args.steps,
+                              "time_steps_per_step": SUB, "kernels_ms": kms, "gpu_launches": int(gpu_launches)}),
+                  flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
 
     # ---------------- end to end through host buffers ----------------
     pin_n = torch.empty(n_h.shape, dtype=torch.float64, pin_memory=True)
@@ -378,9 +386,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-device", action="store_true",
+                    help="time only the device-resident loop (for profiling); no e2e, baseline or other paths")
+    ap.add_argument("--sub", type=int, default=SUB, help="lattice time steps per benchmark step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    global SUB
+    SUB = args.sub
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -76,7 +76,7 @@ void build_shell(double sigma, std::vector<int> &out, double *w)
 }
 
 struct Layout {
-    size_t f[2], nu, hb, cprev, tprev, stage, snap, partial, result, status, shell_e, shell_k, ball, total;
+    size_t f[2], nu, hb, cprev, tprev, nscale, stage, snap, partial, result, status, shell_e, shell_k, ball, total;
 };
 
 int storage_bytes(int storage) { return storage == WDLB_STORE_F64 ? 8 : (storage == WDLB_STORE_F32 ? 4 : 2); }
@@ -98,6 +98,7 @@ Layout layout_for(long long N, long long Npad, int storage, int nshell, int nbal
     L.hb = take(Npad * sT);
     L.cprev = take(3 * Npad * sT);
     L.tprev = take(Npad * sT);
+    L.nscale = take(Npad * sT);
     L.stage = take(4 * N * sizeof(double));
     L.snap = take(N * sizeof(double));
     L.partial = take(kStatBlocks * 6 * sizeof(double));
@@ -223,15 +224,18 @@ void set_params(wdlb_ctx *ctx)
     p.chi_of_n = M_PI * ctx->sigma * ctx->sigma * ctx->sigma / 6.0;
     p.c_half = p.chi_of_n / (2.0 * std::max(p.nball, 1));
     p.h_pred = KAPPA * p.beta / 6.0;
+    const double s2 = 2.0 * ctx->sigma;
+    p.s2 = (std::fabs(s2 - std::round(s2)) < 1e-12) ? (int)std::lround(s2) : 0;
+    p.tiled = 0;
     // n_off / ref_ng are set at init (they may depend on the initial state)
 }
 
 void set_reference(wdlb_ctx *ctx, double n_ref)
 {
     KParams &p = ctx->kp;
-    p.n_off = ctx->opt.storage == WDLB_STORE_F64 ? 0.0 : n_ref;
-    p.inv_n_off = p.n_off > 0 ? 1.0 / p.n_off : 1.0;
+    p.n_off = n_ref;
     p.ref_ng = n_ref * contact_g_host(ctx->opt.closure, p.chi_of_n * n_ref);
+    p.h_off = 0.5 * p.chi_of_n * p.n_off;
 }
 
 void drop_graphs(wdlb_ctx *ctx)
@@ -376,6 +380,7 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
     build_shell(sigma, ctx->tab.shell, &ctx->tab.wshell);
     ctx->L = &launchers_for(o.storage);
     set_params(ctx);
+    ctx->kp.tiled = ctx->L->prepare(ctx->kp) ? 1 : 0;
     set_reference(ctx, o.n_ref > 0 ? o.n_ref : 1.0);
     const int nshell = ctx->kp.nshell, nball = ctx->kp.nball;
     ctx->lay = layout_for(ctx->N, ctx->Npad, o.storage, nshell, nball);
@@ -416,6 +421,7 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
     ctx->dev.hb = b + L.hb;
     ctx->dev.cprev = b + L.cprev;
     ctx->dev.tprev = b + L.tprev;
+    ctx->dev.nscale = b + L.nscale;
     ctx->dev.stage = reinterpret_cast<double *>(b + L.stage);
     ctx->dev.snap = reinterpret_cast<double *>(b + L.snap);
     ctx->dev.partial = reinterpret_cast<double *>(b + L.partial);

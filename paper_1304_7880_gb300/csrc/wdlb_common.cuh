@@ -48,17 +48,19 @@ struct KParams {
     int N, Npad;             // node count, padded stride of per-node arrays
     int nshell, nball;
     int closure, omega_mode, interactions;
+    int s2;                  // 2 sigma if it is an integer, else 0 (selects a compiled shell)
+    int tiled;               // 1: use the shared-memory tiled shell kernel
     double g[3];             // external acceleration
     double omega;            // 1/tau
     double tau;
     double k_cross;          // K of the A-term
     double n_off;            // storage offset density (0 for FP64)
-    double inv_n_off;        // 1/n_off (FP16 scaling), 1 if n_off == 0
     double sig2;             // sigma^2
     double beta;             // 2 sigma^2 sqrt(kT/pi)
     double wshell;           // uniform shell weight
     double chi_of_n;         // pi sigma^3 / 6
     double c_half;           // chi_of_n / (2 |ball|): half packing fraction per ball sum
+    double h_off;            // half packing fraction of n_off: chi_of_n n_off / 2
     double ref_ng;           // n_ref g2(n_ref) (NBAR mode)
     double h_pred;           // kappa beta / 6: implicit factor of the field-velocity predictor per unit t
 };
@@ -68,10 +70,11 @@ template <class S, class T>
 struct KBufs {
     const S *f_in;
     S *f_out;
-    V4<T> *nu;           // (n, v_x, v_y, v_z) per node: density and field velocity
-    T *hb;               // half smeared packing fraction per node
+    V4<T> *nu;           // (n - n_off, v_x, v_y, v_z) per node: density deviation and field velocity
+    T *hb;               // half smeared packing fraction minus h_off, per node
     T *cprev;            // C of the previous step, 3 x Npad
     T *tprev;            // t = sum_e w g2 n(r+e) of the previous step
+    T *nscale;           // storage scale of f_in minus n_off, per node
     const int4 *shell_e; // shell vectors
     const V4<T> *shell_k;// unit vectors e/|e|
     const int4 *ball;    // ball vectors
@@ -98,8 +101,9 @@ inline double contact_g_host(int closure, double chi)
     return (1.5 - 0.5 * s) / (s * s);
 }
 
-// Population storage.  FP64: f itself.  FP32: f - w_q n_off.  FP16:
-// (f - w_q n_off) / (w_q n_off), the relative deviation from the rest state.
+// Population storage relative to a rest state w_q s (s: a density per node).
+// FP64 and FP32: f - w_q s.  FP16: (f - w_q s) / (w_q s).  load() takes the
+// scale w_q s, put() its inverse.
 template <class S>
 struct Store;
 template <>

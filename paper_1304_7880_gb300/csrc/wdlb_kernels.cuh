@@ -1,6 +1,6 @@
 // Kernels of one WDLB time step (Sec. 5, Numerical results: the five-step
-// algorithm), templated on population storage S, closure CL, relaxation mode
-// OM and geometry (WALLS).  Compute type T = Store<S>::T.
+// algorithm), templated on population storage S, closure CL and geometry
+// (WALLS); the relaxation mode is a runtime branch.  Compute type T = Store<S>::T.
 //
 //   k_moments        step 4 of Sec. 5 (Eq. colonna): n, j from f, and the
 //                    field velocity v, a lagged linear-implicit predictor of
@@ -9,6 +9,18 @@
 //                      H = kappa (beta/2) t_prev / 3,  t = sum_e w g2 n(r+e).
 //   k_ball           smeared density of Sec. 3 over the lattice ball, stored
 //                    as half packing fraction chi/2 per node.
+//
+// Deviation form: nu holds n - n_off and hb holds chi/2 - h_off (h_off the
+// value of n_off), so that the mean-field sum, which cancels down to a
+// density gradient, is formed from differences of deviations (see
+// pair_weights) and keeps FP32 accuracy relative to the gradient itself.
+//
+// Population storage is relative to a local rest state: the value stored for
+// f_q(r) is f_q - w_q s(r) (FP64, FP32) or (f_q - w_q s(r)) / (w_q s(r))
+// (FP16), with s(r) = n_off + nscale[r] the density of node r one step
+// earlier.  The pushes of a step encode with the target's current density,
+// which becomes the target's scale for the next step; the stored values stay
+// small near walls, where n departs far from n_off.
 //   k_shell_collide  steps 2 + 3 of Sec. 5: the shell sums of Eq. campoc
 //                    (C = n (F^mf + F^viscous)) and Eq. campod (A) with
 //                    du = v(r+e) - v(r), the collision of Eq. SMDB with the
@@ -45,19 +57,24 @@ __global__ void __launch_bounds__(256) k_init(KParams p, KBufs<S, typename Store
     if (i >= p.N) return;
     int z = i / (p.nx * p.ny);
     bool solid = solid_plane(p, z);
-    T n = solid ? T(0) : T(st_n[i]);
+    // deviations from n_off are formed in FP64 before rounding to T
+    const T dnv = solid ? -T(p.n_off) : T(st_n[i] - p.n_off);
+    T n = solid ? T(0) : T(p.n_off) + dnv;
     T ux = solid || !st_u ? T(0) : T(st_u[i]);
     T uy = solid || !st_u ? T(0) : T(st_u[p.N + i]);
     T uz = solid || !st_u ? T(0) : T(st_u[2 * p.N + i]);
-    T dn = n - T(p.n_off);
-    T uu = ux * ux + uy * uy + uz * uz;
+    // local rest state s(r) = n (solid nodes: n_off, their slots are never read)
+    const T dsc = solid ? T(0) : dnv;
+    const T sc = T(p.n_off) + dsc;
+    const T uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
         T cu = T(cx_of(q)) * ux + T(cy_of(q)) * uy + T(cz_of(q)) * uz;
-        T dev = T(w_of(q)) * (dn + n * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-        Store<S>::put(b.f_out + (size_t)q * p.Npad + i, dev, T(1.0 / w_of(q)) * T(p.inv_n_off));
+        T dev = solid ? T(0) : T(w_of(q)) * n * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+        Store<S>::put(b.f_out + (size_t)q * p.Npad + i, dev, T(1.0 / w_of(q)) / sc);
     }
-    b.nu[i] = V4<T>{n, ux, uy, uz};
+    b.nu[i] = V4<T>{dnv, ux, uy, uz};
+    b.nscale[i] = dsc;
     b.cprev[i] = T(0);
     b.cprev[p.Npad + i] = T(0);
     b.cprev[2 * p.Npad + i] = T(0);
@@ -81,20 +98,23 @@ __global__ void __launch_bounds__(256) k_moments(KParams p, KBufs<S, typename St
             if (out_n) out_n[i] = 0.0;
             if (out_u) out_u[i] = out_u[p.N + i] = out_u[2 * p.N + i] = 0.0;
         } else {
-            b.nu[i] = V4<T>{T(0), T(0), T(0), T(0)};
+            b.nu[i] = V4<T>{-T(p.n_off), T(0), T(0), T(0)};
         }
         return;
     }
     const T noff = T(p.n_off);
-    T dn = T(0), jx = T(0), jy = T(0), jz = T(0);
+    const T dsc = b.nscale[i];
+    const T sc = noff + dsc;
+    T dl = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
-        T d = Store<S>::load(b.f_in + (size_t)q * p.Npad + i, T(w_of(q)) * noff);
-        dn += d;
+        T d = Store<S>::load(b.f_in + (size_t)q * p.Npad + i, T(w_of(q)) * sc);
+        dl += d;
         if (cx_of(q)) jx += T(cx_of(q)) * d;
         if (cy_of(q)) jy += T(cy_of(q)) * d;
         if (cz_of(q)) jz += T(cz_of(q)) * d;
     }
+    const T dn = dsc + dl;          // n - n_off
     const T n = noff + dn;
     if (!(n > T(0)) || !isfinite(n)) atomicOr(b.status, 1);
     const T inv = T(1) / n;
@@ -112,7 +132,7 @@ __global__ void __launch_bounds__(256) k_moments(KParams p, KBufs<S, typename St
             out_u[2 * p.N + i] = double(vz);
         }
     } else {
-        b.nu[i] = V4<T>{n, vx, vy, vz};
+        b.nu[i] = V4<T>{dn, vx, vy, vz};
     }
 }
 
@@ -129,15 +149,19 @@ __global__ void __launch_bounds__(256) k_ball(KParams p, const V4<T> *nu, T *hb,
     int y = (i / p.nx) % p.ny;
     int z = i / (p.nx * p.ny);
     if (solid_plane(p, z)) {
-        hb[i] = T(0);
+        hb[i] = -T(p.h_off);    // n = 0: chi = 0
         return;
     }
-    T sum = T(0);
+    const T noff = T(p.n_off);
+    T sum = T(0);               // sum over the ball of n - n_off
     for (int m = 0; m < p.nball; m++) {
         int4 e = ball[m];
         int zz = z + e.z;
         if (p.walls) {
-            if (zz < 0 || zz >= p.nz) continue;
+            if (zz < 0 || zz >= p.nz) {
+                sum -= noff;    // beyond a wall: n = 0
+                continue;
+            }
         } else {
             zz = wrap_coord(zz, p.nz);
         }
@@ -145,91 +169,128 @@ __global__ void __launch_bounds__(256) k_ball(KParams p, const V4<T> *nu, T *hb,
         int yy = wrap_coord(y + e.y, p.ny);
         sum += nu[xx + p.nx * (yy + p.ny * zz)].x;
     }
-    T h = T(p.c_half) * sum;
-    if (!(h < T(0.5))) atomicOr(status, 1);
-    hb[i] = h;
+    T dh = T(p.c_half) * sum;
+    if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
+    hb[i] = dh;
 }
 
 // ---------------------------------------------------------------------------
-// Fields + collision + streaming, one node per thread.
+// Pair weights of a (+e, -e) pair of the contact shell.  q = g2(chi_mid) n(r+e)
+// (without the quadrature weight), chi_mid/2 = hb(r) + hb(r+e).  s0 = 1 - h(r)
+// - h_off; dh, dn: deviations of the two neighbours.  Besides q+ and q- it
+// returns q+ - q-, formed from the deviations so that it is accurate relative
+// to itself (it is what the mean-field sum accumulates):
+//   q+ - q- = g+ (dn+ - dn-) + (g+ - g-) n-,
+//   CS:  g+ - g- = (dh+ - dh-) [s+^2 + s-^2 + s+ s- (1 + s+ + s-)] / (2 s+^3 s-^3)
+//   PY:  g+ - g- = (dh+ - dh-) [3 (s+ + s-)/2 - s+ s-/2] / (s+^2 s-^2)
+// with s = 1 - chi_mid the argument of g2(chi) = (1 + s)/(2 s^3) (CS) or
+// (3 - s)/(2 s^2) (PY).
 // ---------------------------------------------------------------------------
-template <class S, int CL, int OM, bool WALLS, bool FIELDS>
-__global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typename Store<S>::T> b)
+template <class T>
+__device__ __forceinline__ T fast_rcp(T x);
+template <>
+__device__ __forceinline__ float fast_rcp<float>(float x)
 {
-    typedef typename Store<S>::T T;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.N) return;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    int x = i % nx;
-    int y = (i / nx) % ny;
-    int z = i / (nx * ny);
-    if (WALLS && (z == 0 || z == nz - 1)) return;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <>
+__device__ __forceinline__ double fast_rcp<double>(double x)
+{
+    return 1.0 / x;
+}
 
-    // own populations and moments
-    const T noff = T(p.n_off), inoff = T(p.inv_n_off);
+template <int CL, class T>
+__device__ __forceinline__ void pair_weights(T s0, T noff, T dhp, T dnp, T dhm, T dnm, T &qp, T &qm, T &qd)
+{
+    const T np = noff + dnp, nm = noff + dnm;
+    if (CL == 2) {
+        qp = np;
+        qm = nm;
+        qd = dnp - dnm;
+        return;
+    }
+    const T sp = s0 - dhp, sm = s0 - dhm;
+    const T spm = sp * sm;
+    T gp, gm, gd;
+    if (CL == 0) {
+        const T rp = fast_rcp<T>(sp * sp * sp), rm = fast_rcp<T>(sm * sm * sm);
+        gp = (T(0.5) + T(0.5) * sp) * rp;
+        gm = (T(0.5) + T(0.5) * sm) * rm;
+        gd = (dhp - dhm) * (sp * sp + sm * sm + spm * (T(1) + sp + sm)) * (T(0.5) * rp * rm);
+    } else {
+        const T rp = fast_rcp<T>(sp * sp), rm = fast_rcp<T>(sm * sm);
+        gp = (T(1.5) - T(0.5) * sp) * rp;
+        gm = (T(1.5) - T(0.5) * sm) * rm;
+        gd = (dhp - dhm) * (T(1.5) * (sp + sm) - T(0.5) * spm) * (rp * rm);
+    }
+    qp = gp * np;
+    qm = gm * nm;
+    qd = gp * (dnp - dnm) + gd * nm;
+}
+
+// Shell-sum accumulators (without the quadrature weight w).
+template <class T>
+struct ShellAcc {
+    T Vx, Vy, Vz;                       // sum q khat                      (F^mf)
+    T Wx, Wy, Wz;                       // sum q khat (khat . dv)          (F^viscous)
+    T Sxx, Syy, Szz, Sxy, Sxz, Syz;     // sum q (khat_b dv_a + khat_a dv_b), diagonal counted once (A)
+    T t;                                // sum q                           (predictor)
+};
+
+// Add the (+e, -e) pair with unit vector (kx, ky, kz) of +e.  khat(-e) = -khat(+e):
+// V takes q+ - q-, W the sum of the two ends' q dv, S their difference.
+template <class T>
+__device__ __forceinline__ void accumulate_pair(ShellAcc<T> &a, T kx, T ky, T kz, T qp, T qm, T qd, T vpx, T vpy,
+                                                T vpz, T vmx, T vmy, T vmz, T vx, T vy, T vz)
+{
+    const T px = qp * (vpx - vx), py = qp * (vpy - vy), pz = qp * (vpz - vz);
+    const T mx = qm * (vmx - vx), my = qm * (vmy - vy), mz = qm * (vmz - vz);
+    const T sx = px + mx, sy = py + my, sz = pz + mz;
+    const T dx = px - mx, dy = py - my, dz = pz - mz;
+    a.t += qp + qm;
+    a.Vx += kx * qd; a.Vy += ky * qd; a.Vz += kz * qd;
+    const T ks = kx * sx + ky * sy + kz * sz;
+    a.Wx += kx * ks; a.Wy += ky * ks; a.Wz += kz * ks;
+    a.Sxx += kx * dx; a.Syy += ky * dy; a.Szz += kz * dz;
+    a.Sxy += ky * dx + kx * dy;
+    a.Sxz += kz * dx + kx * dz;
+    a.Syz += kz * dy + ky * dz;
+}
+
+// ---------------------------------------------------------------------------
+// Collision and push streaming of node i (step 3 of Sec. 5), given its fields.
+// C = n (F^mf + F^viscous) (Eq. campoc); A (Eq. campod, not yet traceless);
+// tsum = t of the field-velocity predictor for the next step.  FIELDS: write
+// nbar, C, A and the collision velocity instead of advancing the state.
+// ---------------------------------------------------------------------------
+// target_dn(q, dst) returns n - n_off of the node a population is pushed to
+// (this step's density there: its storage scale for the next step).
+template <class S, int CL, bool WALLS, bool FIELDS, class T, class TargetDn>
+__device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T> &b, int i, int x, int y, int z,
+                                             T hr, T Cx, T Cy, T Cz, T Axx, T Ayy, T Azz, T Axy, T Axz, T Ayz,
+                                             T tsum, T dn_self, TargetDn target_dn)
+{
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const T noff = T(p.n_off);
+    const T dsc = b.nscale[i];           // this node's storage scale - n_off
+    const T sc = noff + dsc;
     T d[NQ];
-    T dn = T(0), jx = T(0), jy = T(0), jz = T(0);
+    T dn = T(0), jx = T(0), jy = T(0), jz = T(0);   // dn: n - s(r)
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
-        d[q] = Store<S>::load(b.f_in + (size_t)q * p.Npad + i, T(w_of(q)) * noff);
+        d[q] = Store<S>::load(b.f_in + (size_t)q * p.Npad + i, T(w_of(q)) * sc);
         dn += d[q];
         if (cx_of(q)) jx += T(cx_of(q)) * d[q];
         if (cy_of(q)) jy += T(cy_of(q)) * d[q];
         if (cz_of(q)) jz += T(cz_of(q)) * d[q];
     }
-    const T n = noff + dn;
+    const T n = sc + dn;
     const T inv_n = T(1) / n;
-    const T gx = T(p.g[0]), gy = T(p.g[1]), gz = T(p.g[2]);
-    const T hr = b.hb[i];
-    const V4<T> me = b.nu[i];
-    const T vx = me.y, vy = me.z, vz = me.w;
-
-    T Cx = T(0), Cy = T(0), Cz = T(0);
-    T Axx = T(0), Ayy = T(0), Azz = T(0), Axy = T(0), Axz = T(0), Ayz = T(0);
-    T tsum = T(0);
-    if (p.interactions) {
-        T Vx = T(0), Vy = T(0), Vz = T(0);       // sum q khat           (F^mf)
-        T Wx = T(0), Wy = T(0), Wz = T(0);       // sum q khat (khat.dv) (F^visc)
-        T Sxx = T(0), Syy = T(0), Szz = T(0), Sxy = T(0), Sxz = T(0), Syz = T(0);
-        for (int m = 0; m < p.nshell; m++) {
-            const int4 e = b.shell_e[m];
-            const V4<T> k = b.shell_k[m];
-            int zz = z + e.z;
-            if (WALLS) {
-                if (zz <= 0 || zz >= nz - 1) continue;   // solid or beyond: n = 0
-            } else {
-                zz = wrap_coord(zz, nz);
-            }
-            const int xx = wrap_coord(x + e.x, nx);
-            const int yy = wrap_coord(y + e.y, ny);
-            const int j = xx + nx * (yy + ny * zz);
-            const V4<T> ne = b.nu[j];
-            const T q = contact_g<CL, T>(hr + b.hb[j]) * ne.x;
-            const T dvx = ne.y - vx, dvy = ne.z - vy, dvz = ne.w - vz;
-            const T qkd = q * (k.x * dvx + k.y * dvy + k.z * dvz);
-            Vx += q * k.x; Vy += q * k.y; Vz += q * k.z;
-            Wx += qkd * k.x; Wy += qkd * k.y; Wz += qkd * k.z;
-            const T qx = q * dvx, qy = q * dvy, qz = q * dvz;
-            Sxx += k.x * qx; Syy += k.y * qy; Szz += k.z * qz;
-            Sxy += k.y * qx + k.x * qy;
-            Sxz += k.z * qx + k.x * qz;
-            Syz += k.z * qy + k.y * qz;
-            tsum += q;
-        }
-        const T w = T(p.wshell);
-        const T mf = -T(CS2) * T(p.sig2) * w * n;
-        const T vi = T(p.beta) * w * n;
-        Cx = mf * Vx + vi * Wx;
-        Cy = mf * Vy + vi * Wy;
-        Cz = mf * Vz + vi * Wz;
-        const T pa = -(T(CS2) / T(5)) * T(p.sig2) * n * w;
-        Axx = T(2) * pa * Sxx; Ayy = T(2) * pa * Syy; Azz = T(2) * pa * Szz;
-        Axy = pa * Sxy; Axz = pa * Sxz; Ayz = pa * Syz;
-        tsum *= w;
-    }
 
     // collision velocity u = (j + F/2)/n with F = n g + C
-    const T Fx = n * gx + Cx, Fy = n * gy + Cy, Fz = n * gz + Cz;
+    const T Fx = n * T(p.g[0]) + Cx, Fy = n * T(p.g[1]) + Cy, Fz = n * T(p.g[2]) + Cz;
     const T ux = (jx + T(0.5) * Fx) * inv_n;
     const T uy = (jy + T(0.5) * Fy) * inv_n;
     const T uz = (jz + T(0.5) * Fz) * inv_n;
@@ -246,7 +307,7 @@ __global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typen
 
     // relaxation frequency
     T omega = T(p.omega);
-    if (OM == 1) {
+    if (p.omega_mode == 1) {
         const T chib = T(2) * hr;
         const T loc = chib / T(p.chi_of_n) * contact_g<CL, T>(chib);
         T tau = loc > T(0) ? T(0.5) + (T(p.tau) - T(0.5)) * T(p.ref_ng) / loc : T(1e30);
@@ -274,21 +335,27 @@ __global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typen
                       T(2 * cxq * cyq) * Axy + T(2 * cxq * czq) * Axz + T(2 * cyq * czq) * Ayz;
         const T sa = kA * wq * cAc;
         const T post = d[q] - omega * (d[q] - feq_dev) + src_pref * (phi + sa);
-        // push streaming with half-way bounce-back
+        // push streaming with half-way bounce-back; re-encode relative to the
+        // target's rest state w_q s(target), s(target) = its density now
         int zt = z + czq;
         int dst;
         int qq = q;
+        T dn_t;
         if (WALLS && (zt == 0 || zt == nz - 1)) {
             dst = i;
             qq = opp_of(q);
+            dn_t = dn_self;
         } else {
             if (!WALLS) zt = wrap_coord(zt, nz);
             const int xt = wrap_coord(x + cxq, nx);
             const int yt = wrap_coord(y + cyq, ny);
             dst = xt + nx * (yt + ny * zt);
+            dn_t = q == 0 ? dn_self : target_dn(q, dst);
         }
-        Store<S>::put(b.f_out + (size_t)qq * p.Npad + dst, post, T(1.0 / w_of(q)) * inoff);
+        const T stored = post + wq * (dsc - dn_t);
+        Store<S>::put(b.f_out + (size_t)qq * p.Npad + dst, stored, T(1.0 / w_of(q)) * fast_rcp<T>(noff + dn_t));
     }
+    b.nscale[i] = dn_self;
     b.cprev[i] = Cx;
     b.cprev[p.Npad + i] = Cy;
     b.cprev[2 * p.Npad + i] = Cz;
@@ -296,10 +363,84 @@ __global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typen
 }
 
 // ---------------------------------------------------------------------------
+// Fields + collision + streaming, one node per thread, shell table from
+// global memory (any sigma and lattice shape).
+// ---------------------------------------------------------------------------
+template <class S, int CL, bool WALLS, bool FIELDS>
+__global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typename Store<S>::T> b)
+{
+    typedef typename Store<S>::T T;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    int x = i % nx;
+    int y = (i / nx) % ny;
+    int z = i / (nx * ny);
+    if (WALLS && (z == 0 || z == nz - 1)) return;
+
+    const T noff = T(p.n_off), hoff = T(p.h_off);
+    const T dhr = b.hb[i];
+    const T hr = hoff + dhr;
+    const V4<T> me = b.nu[i];
+    const T n = noff + me.x;
+    const T vx = me.y, vy = me.z, vz = me.w;
+
+    T Cx = T(0), Cy = T(0), Cz = T(0);
+    T Axx = T(0), Ayy = T(0), Azz = T(0), Axy = T(0), Axz = T(0), Ayz = T(0);
+    T tsum = T(0);
+    if (p.interactions) {
+        ShellAcc<T> a = {};
+        const T s0 = T(1) - hr - hoff;
+        for (int m = 0; m + 1 < p.nshell; m += 2) {     // (+e, -e) pairs
+            const int4 e = b.shell_e[m];
+            const V4<T> k = b.shell_k[m];
+            V4<T> nb[2];
+            T hbv[2];
+            for (int side = 0; side < 2; side++) {
+                const int sg = side == 0 ? 1 : -1;
+                int zz = z + sg * e.z;
+                bool solid = false;
+                if (WALLS)
+                    solid = zz <= 0 || zz >= nz - 1;   // solid or beyond: n = 0
+                else
+                    zz = wrap_coord(zz, nz);
+                if (solid) {
+                    nb[side] = V4<T>{-noff, T(0), T(0), T(0)};
+                    hbv[side] = -hoff;
+                } else {
+                    const int xx = wrap_coord(x + sg * e.x, nx);
+                    const int yy = wrap_coord(y + sg * e.y, ny);
+                    const int j = xx + nx * (yy + ny * zz);
+                    nb[side] = b.nu[j];
+                    hbv[side] = b.hb[j];
+                }
+            }
+            T qp, qm, qd;
+            pair_weights<CL, T>(s0, noff, hbv[0], nb[0].x, hbv[1], nb[1].x, qp, qm, qd);
+            accumulate_pair<T>(a, k.x, k.y, k.z, qp, qm, qd, nb[0].y, nb[0].z, nb[0].w, nb[1].y, nb[1].z, nb[1].w,
+                               vx, vy, vz);
+        }
+        const T w = T(p.wshell);
+        const T mf = -T(CS2) * T(p.sig2) * w * n;
+        const T vi = T(p.beta) * w * n;
+        Cx = mf * a.Vx + vi * a.Wx;
+        Cy = mf * a.Vy + vi * a.Wy;
+        Cz = mf * a.Vz + vi * a.Wz;
+        const T pa = -(T(CS2) / T(5)) * T(p.sig2) * n * w;
+        Axx = T(2) * pa * a.Sxx; Ayy = T(2) * pa * a.Syy; Azz = T(2) * pa * a.Szz;
+        Axy = pa * a.Sxy; Axz = pa * a.Sxz; Ayz = pa * a.Syz;
+        tsum = a.t * w;
+    }
+    collide_push<S, CL, WALLS, FIELDS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
+                                       [&](int, int dst) { return b.nu[dst].x; });
+}
+
+// ---------------------------------------------------------------------------
 // Outputs and FP64 reductions.
 // ---------------------------------------------------------------------------
 template <class S>
-__global__ void __launch_bounds__(256) k_pop_to_f64(KParams p, const S *f, int q, double *out)
+__global__ void __launch_bounds__(256) k_pop_to_f64(KParams p, const S *f, const typename Store<S>::T *nscale, int q,
+                                                    double *out)
 {
     typedef typename Store<S>::T T;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -309,8 +450,9 @@ __global__ void __launch_bounds__(256) k_pop_to_f64(KParams p, const S *f, int q
         out[i] = 0.0;
         return;
     }
-    T dv = Store<S>::load(f + (size_t)q * p.Npad + i, T(w_of(q)) * T(p.n_off));
-    out[i] = double(dv) + w_of(q) * p.n_off;
+    const T sc = T(p.n_off) + nscale[i];
+    T dv = Store<S>::load(f + (size_t)q * p.Npad + i, T(w_of(q)) * sc);
+    out[i] = double(dv) + w_of(q) * double(sc);
 }
 
 // Per-block FP64 partial sums over fluid nodes of the FP64 moments n, u_x:

@@ -2,6 +2,7 @@
 // WDLB_STORAGE (0: FP64, 1: FP32 deviation, 2: FP16 relative deviation).
 #include "wdlb_kernels.cuh"
 #include "wdlb_launch.h"
+#include "wdlb_shell_tiled.cuh"
 
 #ifndef WDLB_STORAGE
 #error "compile with -DWDLB_STORAGE=0|1|2"
@@ -32,6 +33,7 @@ KBufs<S, T> typed(const DevBufs &d, int cur)
     b.hb = static_cast<T *>(d.hb);
     b.cprev = static_cast<T *>(d.cprev);
     b.tprev = static_cast<T *>(d.tprev);
+    b.nscale = static_cast<T *>(d.nscale);
     b.shell_e = d.shell_e;
     b.shell_k = static_cast<const V4<T> *>(d.shell_k);
     b.ball = d.ball;
@@ -40,23 +42,92 @@ KBufs<S, T> typed(const DevBufs &d, int cur)
     return b;
 }
 
-template <int CL, int OM, bool WALLS, bool FIELDS>
+template <int CL, bool WALLS, bool FIELDS>
 void launch_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
 {
-    k_shell_collide<S, CL, OM, WALLS, FIELDS><<<blocks_for(p.N), kThreads, 0, st>>>(p, b);
+    k_shell_collide<S, CL, WALLS, FIELDS><<<blocks_for(p.N), kThreads, 0, st>>>(p, b);
+}
+
+#if WDLB_STORAGE != 0
+// The tiled kernel is compiled for the Carnahan-Starling closure (the default)
+// and sigma in {3, 4, 6}; other closures and sigmas use k_shell_collide.
+template <int S2, bool WALLS>
+cudaError_t tiled_attr()
+{
+    return cudaFuncSetAttribute(tiled::k_shell_tiled<S, S2, 0, WALLS, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled::smem_bytes<S2>());
+}
+
+template <int S2, bool WALLS>
+void launch_tiled(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
+{
+    dim3 grid((p.nx + tiled::TX - 1) / tiled::TX, (p.ny + tiled::TY - 1) / tiled::TY,
+              (p.nz + tiled::TZ - 1) / tiled::TZ);
+    tiled::k_shell_tiled<S, S2, 0, WALLS, false><<<grid, tiled::THREADS, tiled::smem_bytes<S2>(), st>>>(p, b);
+}
+
+template <int S2>
+void tiled_s2(const KParams &p, const KBufs<S, T> *b, cudaStream_t st, cudaError_t *attr)
+{
+    if (p.walls) {
+        if (attr) *attr = tiled_attr<S2, true>();
+        else launch_tiled<S2, true>(p, *b, st);
+    } else {
+        if (attr) *attr = tiled_attr<S2, false>();
+        else launch_tiled<S2, false>(p, *b, st);
+    }
+}
+
+// attr != nullptr: set kernel attributes instead of launching
+void dispatch_tiled(const KParams &p, const KBufs<S, T> *b, cudaStream_t st, cudaError_t *attr)
+{
+    switch (p.s2) {
+    case 6: tiled_s2<6>(p, b, st, attr); break;
+    case 8: tiled_s2<8>(p, b, st, attr); break;
+    case 12: tiled_s2<12>(p, b, st, attr); break;
+    default: break;
+    }
+}
+#endif
+
+bool tiled_eligible(const KParams &p)
+{
+#if WDLB_STORAGE != 0
+    return (p.s2 == 6 || p.s2 == 8 || p.s2 == 12) && p.closure == 0 && p.nx >= tiled::TX && p.ny >= tiled::TY;
+#else
+    (void)p;
+    return false;
+#endif
+}
+
+bool do_prepare(const KParams &p)
+{
+    if (!tiled_eligible(p)) return false;
+#if WDLB_STORAGE != 0
+    cudaError_t e = cudaSuccess;
+    dispatch_tiled(p, nullptr, nullptr, &e);
+    return e == cudaSuccess;
+#else
+    return false;
+#endif
 }
 
 template <bool FIELDS>
 void dispatch_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
 {
-#define WDLB_CASE(CL, OM, W)                                            \
-    if (p.closure == CL && p.omega_mode == OM && (p.walls != 0) == W) { \
-        launch_shell<CL, OM, W, FIELDS>(p, b, st);                      \
-        return;                                                         \
+#if WDLB_STORAGE != 0
+    if (!FIELDS && p.tiled) {
+        dispatch_tiled(p, &b, st, nullptr);
+        return;
     }
-    WDLB_CASE(0, 0, true) WDLB_CASE(0, 0, false) WDLB_CASE(0, 1, true) WDLB_CASE(0, 1, false)
-    WDLB_CASE(1, 0, true) WDLB_CASE(1, 0, false) WDLB_CASE(1, 1, true) WDLB_CASE(1, 1, false)
-    WDLB_CASE(2, 0, true) WDLB_CASE(2, 0, false) WDLB_CASE(2, 1, true) WDLB_CASE(2, 1, false)
+#endif
+#define WDLB_CASE(CL, W)                                \
+    if (p.closure == CL && (p.walls != 0) == W) {       \
+        launch_shell<CL, W, FIELDS>(p, b, st);          \
+        return;                                         \
+    }
+    WDLB_CASE(0, true) WDLB_CASE(0, false) WDLB_CASE(1, true) WDLB_CASE(1, false) WDLB_CASE(2, true)
+    WDLB_CASE(2, false)
 #undef WDLB_CASE
 }
 
@@ -123,7 +194,8 @@ cudaError_t do_moments(const KParams &p, const DevBufs &d, int cur, double *d_n,
 cudaError_t do_population(const KParams &p, const DevBufs &d, int cur, int q, double *out, cudaStream_t st,
                           int64_t *launches)
 {
-    k_pop_to_f64<S><<<blocks_for(p.N), kThreads, 0, st>>>(p, static_cast<const S *>(d.f[cur]), q, out);
+    k_pop_to_f64<S><<<blocks_for(p.N), kThreads, 0, st>>>(p, static_cast<const S *>(d.f[cur]),
+                                                          static_cast<const T *>(d.nscale), q, out);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -140,7 +212,7 @@ cudaError_t do_stats(const KParams &p, const DevBufs &d, int cur, int update_sna
     return cudaGetLastError();
 }
 
-const Launchers kL = {do_init, do_step, do_step_part, do_fields, do_moments, do_population, do_stats};
+const Launchers kL = {do_prepare, do_init, do_step, do_step_part, do_fields, do_moments, do_population, do_stats};
 
 }  // namespace
 

@@ -18,6 +18,7 @@ struct DevBufs {
     void *hb;            // T per node
     void *cprev;         // 3 x Npad T
     void *tprev;         // Npad T
+    void *nscale;        // Npad T
     const int4 *shell_e;
     const void *shell_k; // V4<T> per shell vector
     const int4 *ball;
@@ -31,6 +32,9 @@ struct DevBufs {
 constexpr int kStatBlocks = 304;
 
 struct Launchers {
+    // per-context preparation outside any stream capture (kernel attributes);
+    // returns whether the tiled shell kernel can serve these parameters
+    bool (*prepare)(const KParams &);
     cudaError_t (*init)(const KParams &, const DevBufs &, int cur, const double *d_n, const double *d_u,
                         cudaStream_t, int64_t *launches);
     // one time step from buffer `cur` into `cur ^ 1`

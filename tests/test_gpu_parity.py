@@ -193,7 +193,9 @@ def test_steady_state_poiseuille(w):
     z = np.arange(1, nz - 1)
     np.testing.assert_allclose(u[0, 1:-1, 0, 0], g / (2 * nu) * (z - 0.5) * (nz - 1.5 - z), rtol=1e-7)
     st = w.wdlb_pore_average(ctx)
-    assert st["eta_eff"] == pytest.approx(0.01 * nu, rel=1e-3)
+    # node average of the parabola over z = 1..H: (g/2nu)(H^2/6 + 1/12), H = nz - 2
+    H = nz - 2
+    assert st["eta_eff"] == pytest.approx(0.01 * nu * H * H / (H * H + 0.5), rel=1e-6)
 
 
 def test_graph_replay_equals_direct_launches(w):
