@@ -380,6 +380,7 @@ def run_ours(args):
 
 
 def main():
+    global SUB
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -392,7 +393,6 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    global SUB
     SUB = args.sub
     if args.impl == "reference":
         return run_reference(args)

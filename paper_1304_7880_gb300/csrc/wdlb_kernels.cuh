@@ -230,6 +230,36 @@ __device__ __forceinline__ void pair_weights(T s0, T noff, T dhp, T dnp, T dhm, 
     qd = gp * (dnp - dnm) + gd * nm;
 }
 
+// q(A) - q(B) for two neighbours A, B of the same node from their deviations:
+// g_A (dn_A - dn_B) + n_B (g_A - g_B), with g_A - g_B as in pair_weights.
+// sA, sB: 1 - chi_mid; rA, rB: 1/sA^3, 1/sB^3 (CS) or 1/sA^2, 1/sB^2 (PY);
+// gA: g2 at A; nB = n_off + dn_B.
+template <int CL, class T>
+__device__ __forceinline__ T q_difference(T dnA, T dhA, T sA, T rA, T gA, T dnB, T dhB, T sB, T rB, T nB)
+{
+    if (CL == 2) return dnA - dnB;
+    const T sAB = sA * sB;
+    const T gd = CL == 0 ? (dhA - dhB) * (sA * sA + sB * sB + sAB * (T(1) + sA + sB)) * (T(0.5) * rA * rB)
+                         : (dhA - dhB) * (T(1.5) * (sA + sB) - T(0.5) * sAB) * (rA * rB);
+    return gA * (dnA - dnB) + gd * nB;
+}
+
+// Contact value g2 from s = 1 - chi_mid, with r = 1/s^3 (CS) or 1/s^2 (PY).
+template <int CL, class T>
+__device__ __forceinline__ T g_from_s(T s, T &r)
+{
+    if (CL == 2) {
+        r = T(1);
+        return T(1);
+    }
+    if (CL == 0) {
+        r = fast_rcp<T>(s * s * s);
+        return (T(0.5) + T(0.5) * s) * r;
+    }
+    r = fast_rcp<T>(s * s);
+    return (T(1.5) - T(0.5) * s) * r;
+}
+
 // Shell-sum accumulators (without the quadrature weight w).
 template <class T>
 struct ShellAcc {
@@ -391,30 +421,30 @@ __global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typen
     if (p.interactions) {
         ShellAcc<T> a = {};
         const T s0 = T(1) - hr - hoff;
+        // neighbour r + sg*e: (n - n_off, v) and hb deviation; solid or beyond a wall: n = 0
+        auto fetch = [&](int ex, int ey, int ez, V4<T> &nb, T &hbv) {
+            int zz = z + ez;
+            bool solid = false;
+            if (WALLS)
+                solid = zz <= 0 || zz >= nz - 1;
+            else
+                zz = wrap_coord(zz, nz);
+            if (solid) {
+                nb = V4<T>{-noff, T(0), T(0), T(0)};
+                hbv = -hoff;
+            } else {
+                const int j = wrap_coord(x + ex, nx) + nx * (wrap_coord(y + ey, ny) + ny * zz);
+                nb = b.nu[j];
+                hbv = b.hb[j];
+            }
+        };
         for (int m = 0; m + 1 < p.nshell; m += 2) {     // (+e, -e) pairs
             const int4 e = b.shell_e[m];
             const V4<T> k = b.shell_k[m];
             V4<T> nb[2];
             T hbv[2];
-            for (int side = 0; side < 2; side++) {
-                const int sg = side == 0 ? 1 : -1;
-                int zz = z + sg * e.z;
-                bool solid = false;
-                if (WALLS)
-                    solid = zz <= 0 || zz >= nz - 1;   // solid or beyond: n = 0
-                else
-                    zz = wrap_coord(zz, nz);
-                if (solid) {
-                    nb[side] = V4<T>{-noff, T(0), T(0), T(0)};
-                    hbv[side] = -hoff;
-                } else {
-                    const int xx = wrap_coord(x + sg * e.x, nx);
-                    const int yy = wrap_coord(y + sg * e.y, ny);
-                    const int j = xx + nx * (yy + ny * zz);
-                    nb[side] = b.nu[j];
-                    hbv[side] = b.hb[j];
-                }
-            }
+            fetch(e.x, e.y, e.z, nb[0], hbv[0]);
+            fetch(-e.x, -e.y, -e.z, nb[1], hbv[1]);
             T qp, qm, qd;
             pair_weights<CL, T>(s0, noff, hbv[0], nb[0].x, hbv[1], nb[1].x, qp, qm, qd);
             accumulate_pair<T>(a, k.x, k.y, k.z, qp, qm, qd, nb[0].y, nb[0].z, nb[0].w, nb[1].y, nb[1].z, nb[1].w,
