@@ -86,11 +86,11 @@ __global__ void __launch_bounds__(256) k_init(KParams p, KBufs<S, typename Store
 // time step); OUT = true: FP64 outputs only, state untouched.
 // ---------------------------------------------------------------------------
 template <class S, bool OUT>
-__global__ void __launch_bounds__(256) k_moments(KParams p, KBufs<S, typename Store<S>::T> b, double *out_n,
-                                                 double *out_u)
+__device__ __forceinline__ void moments_body(const KParams &p, const KBufs<S, typename Store<S>::T> &b, int blk,
+                                             double *out_n, double *out_u)
 {
     typedef typename Store<S>::T T;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blk * blockDim.x + threadIdx.x;
     if (i >= p.N) return;
     int z = i / (p.nx * p.ny);
     if (solid_plane(p, z)) {
@@ -136,14 +136,22 @@ __global__ void __launch_bounds__(256) k_moments(KParams p, KBufs<S, typename St
     }
 }
 
+template <class S, bool OUT>
+__global__ void __launch_bounds__(256) k_moments(KParams p, KBufs<S, typename Store<S>::T> b, double *out_n,
+                                                 double *out_u)
+{
+    moments_body<S, OUT>(p, b, blockIdx.x, out_n, out_u);
+}
+
 // ---------------------------------------------------------------------------
 // Smeared density (Sec. 3) as half packing fraction: hb = (pi s^3/6) nbar / 2.
 // Solid nodes get 0 (they carry n = 0 and never enter a pair with weight).
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) k_ball(KParams p, const V4<T> *nu, T *hb, const int4 *ball, int *status)
+__device__ __forceinline__ void ball_body(const KParams &p, const V4<T> *nu, T *hb, const int4 *ball, int *status,
+                                          int blk)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blk * blockDim.x + threadIdx.x;
     if (i >= p.N) return;
     int x = i % p.nx;
     int y = (i / p.nx) % p.ny;
@@ -172,6 +180,12 @@ __global__ void __launch_bounds__(256) k_ball(KParams p, const V4<T> *nu, T *hb,
     T dh = T(p.c_half) * sum;
     if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
     hb[i] = dh;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_ball(KParams p, const V4<T> *nu, T *hb, const int4 *ball, int *status)
+{
+    ball_body<T>(p, nu, hb, ball, status, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -397,10 +411,10 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
 // global memory (any sigma and lattice shape).
 // ---------------------------------------------------------------------------
 template <class S, int CL, bool WALLS, bool FIELDS>
-__global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typename Store<S>::T> b)
+__device__ __forceinline__ void shell_body(const KParams &p, const KBufs<S, typename Store<S>::T> &b, int blk)
 {
     typedef typename Store<S>::T T;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blk * blockDim.x + threadIdx.x;
     if (i >= p.N) return;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     int x = i % nx;
@@ -463,6 +477,12 @@ __global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typen
     }
     collide_push<S, CL, WALLS, FIELDS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
                                        [&](int, int dst) { return b.nu[dst].x; });
+}
+
+template <class S, int CL, bool WALLS, bool FIELDS>
+__global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typename Store<S>::T> b)
+{
+    shell_body<S, CL, WALLS, FIELDS>(p, b, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------

@@ -44,7 +44,7 @@ constexpr size_t smem_bytes()
 }
 
 template <class S, int S2, int CL, bool WALLS, bool FIELDS>
-__global__ void __launch_bounds__(THREADS, 2) k_shell_tiled(KParams p, KBufs<S, float> b)
+__device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, float> &b, int bx, int by, int bz)
 {
     constexpr int R = shell_radius(S2);
     constexpr int SX = TX + 2 * R, SY = TY + 2 * R, SZ = TZ + 2 * R;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_shell_tiled(KParams p, KBufs<S, 
     float *smh = reinterpret_cast<float *>(smem_raw + sizeof(float4) * (NS + NPAIR));
 
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
 
     // shell pairs: +e is entry 2m of the library's table (-e is 2m + 1)
     for (int m = threadIdx.x; m < NPAIR; m += THREADS) {
@@ -135,6 +135,12 @@ __global__ void __launch_bounds__(THREADS, 2) k_shell_tiled(KParams p, KBufs<S, 
             p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
             [&](int q, int) { return sm4[base + cx_of(q) + SX * (cy_of(q) + SY * cz_of(q))].x; });
     }
+}
+
+template <class S, int S2, int CL, bool WALLS, bool FIELDS>
+__global__ void __launch_bounds__(THREADS, 2) k_shell_tiled(KParams p, KBufs<S, float> b)
+{
+    tiled_body<S, S2, CL, WALLS, FIELDS>(p, b, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace tiled
