@@ -16,6 +16,7 @@
 
 #include "../../include/wdlb.h"
 #include "wdlb_launch.h"
+#include "wdlb_tables.h"
 
 using namespace wdlb;
 
@@ -33,47 +34,6 @@ struct Tables {
     std::vector<int> shell;   // 3 per vector, +e and -e adjacent
     double wshell = 0.0;
 };
-
-void build_ball(double sigma, std::vector<int> &out)
-{
-    out.clear();
-    const double r2 = 0.25 * sigma * sigma;
-    const int R = (int)std::floor(0.5 * sigma);
-    for (int dx = -R; dx <= R; dx++)
-        for (int dy = -R; dy <= R; dy++)
-            for (int dz = -R; dz <= R; dz++)
-                if (double(dx * dx + dy * dy + dz * dz) <= r2) {
-                    out.push_back(dx);
-                    out.push_back(dy);
-                    out.push_back(dz);
-                }
-}
-
-// Shell vectors ordered as (+e, -e) pairs with +e lexicographically positive;
-// weight w such that sigma^2 * sum_e w e_z^2/|e| = 4 pi sigma^3 / 3.
-void build_shell(double sigma, std::vector<int> &out, double *w)
-{
-    out.clear();
-    const double lo = (sigma - 0.5) * (sigma - 0.5), hi = (sigma + 0.5) * (sigma + 0.5);
-    const int R = (int)std::floor(sigma + 0.5);
-    double second = 0.0;
-    for (int dx = 0; dx <= R; dx++)
-        for (int dy = -R; dy <= R; dy++)
-            for (int dz = -R; dz <= R; dz++) {
-                bool positive = dx > 0 || (dx == 0 && (dy > 0 || (dy == 0 && dz > 0)));
-                if (!positive) continue;
-                double r2 = double(dx * dx + dy * dy + dz * dz);
-                if (!(r2 > lo && r2 <= hi)) continue;
-                int v[2][3] = {{dx, dy, dz}, {-dx, -dy, -dz}};
-                for (auto &e : v) {
-                    out.push_back(e[0]);
-                    out.push_back(e[1]);
-                    out.push_back(e[2]);
-                }
-                second += 2.0 * double(dz * dz) / std::sqrt(r2);
-            }
-    *w = second > 0 ? (4.0 * M_PI / 3.0) * sigma / second : 0.0;
-}
 
 struct Layout {
     size_t f[2], nu, hb, cprev, tprev, nscale, stage, snap, partial, result, status, shell_e, shell_k, ball, total;
@@ -697,3 +657,4 @@ void wdlb_destroy(wdlb_ctx *ctx)
 }
 
 }  // extern "C"
+

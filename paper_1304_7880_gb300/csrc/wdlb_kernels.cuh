@@ -406,6 +406,48 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
     b.tprev[i] = tsum;
 }
 
+// Shell sums of node (x, y, z) with the table in global memory (any sigma,
+// any lattice shape): the (+e, -e) pairs of the library's table, neighbours
+// wrapped periodically in x, y (and z without walls), n = 0 on and beyond the
+// walls.  nu, hb in deviation form (see above).
+template <int CL, bool WALLS, class T>
+__device__ __forceinline__ void shell_sums_generic(const KParams &p, const V4<T> *nu, const T *hb,
+                                                   const int4 *shell_e, const V4<T> *shell_k, int x, int y, int z,
+                                                   T hr, T vx, T vy, T vz, ShellAcc<T> &a)
+{
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const T noff = T(p.n_off), hoff = T(p.h_off);
+    const T s0 = T(1) - hr - hoff;
+    auto fetch = [&](int ex, int ey, int ez, V4<T> &nb, T &hbv) {
+        int zz = z + ez;
+        bool solid = false;
+        if (WALLS)
+            solid = zz <= 0 || zz >= nz - 1;
+        else
+            zz = wrap_coord(zz, nz);
+        if (solid) {
+            nb = V4<T>{-noff, T(0), T(0), T(0)};
+            hbv = -hoff;
+        } else {
+            const int j = wrap_coord(x + ex, nx) + nx * (wrap_coord(y + ey, ny) + ny * zz);
+            nb = nu[j];
+            hbv = hb[j];
+        }
+    };
+    for (int m = 0; m + 1 < p.nshell; m += 2) {     // (+e, -e) pairs
+        const int4 e = shell_e[m];
+        const V4<T> k = shell_k[m];
+        V4<T> nb[2];
+        T hbv[2];
+        fetch(e.x, e.y, e.z, nb[0], hbv[0]);
+        fetch(-e.x, -e.y, -e.z, nb[1], hbv[1]);
+        T qp, qm, qd;
+        pair_weights<CL, T>(s0, noff, hbv[0], nb[0].x, hbv[1], nb[1].x, qp, qm, qd);
+        accumulate_pair<T>(a, k.x, k.y, k.z, qp, qm, qd, nb[0].y, nb[0].z, nb[0].w, nb[1].y, nb[1].z, nb[1].w, vx,
+                           vy, vz);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Fields + collision + streaming, one node per thread, shell table from
 // global memory (any sigma and lattice shape).
@@ -434,36 +476,7 @@ __device__ __forceinline__ void shell_body(const KParams &p, const KBufs<S, type
     T tsum = T(0);
     if (p.interactions) {
         ShellAcc<T> a = {};
-        const T s0 = T(1) - hr - hoff;
-        // neighbour r + sg*e: (n - n_off, v) and hb deviation; solid or beyond a wall: n = 0
-        auto fetch = [&](int ex, int ey, int ez, V4<T> &nb, T &hbv) {
-            int zz = z + ez;
-            bool solid = false;
-            if (WALLS)
-                solid = zz <= 0 || zz >= nz - 1;
-            else
-                zz = wrap_coord(zz, nz);
-            if (solid) {
-                nb = V4<T>{-noff, T(0), T(0), T(0)};
-                hbv = -hoff;
-            } else {
-                const int j = wrap_coord(x + ex, nx) + nx * (wrap_coord(y + ey, ny) + ny * zz);
-                nb = b.nu[j];
-                hbv = b.hb[j];
-            }
-        };
-        for (int m = 0; m + 1 < p.nshell; m += 2) {     // (+e, -e) pairs
-            const int4 e = b.shell_e[m];
-            const V4<T> k = b.shell_k[m];
-            V4<T> nb[2];
-            T hbv[2];
-            fetch(e.x, e.y, e.z, nb[0], hbv[0]);
-            fetch(-e.x, -e.y, -e.z, nb[1], hbv[1]);
-            T qp, qm, qd;
-            pair_weights<CL, T>(s0, noff, hbv[0], nb[0].x, hbv[1], nb[1].x, qp, qm, qd);
-            accumulate_pair<T>(a, k.x, k.y, k.z, qp, qm, qd, nb[0].y, nb[0].z, nb[0].w, nb[1].y, nb[1].z, nb[1].w,
-                               vx, vy, vz);
-        }
+        shell_sums_generic<CL, WALLS, T>(p, b.nu, b.hb, b.shell_e, b.shell_k, x, y, z, hr, vx, vy, vz, a);
         const T w = T(p.wshell);
         const T mf = -T(CS2) * T(p.sig2) * w * n;
         const T vi = T(p.beta) * w * n;
