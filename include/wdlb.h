@@ -183,6 +183,35 @@ wdlb_status wdlb_stencil(double sigma, int32_t which, int32_t *vecs, int32_t cap
  * streaming.  Synchronous. */
 wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3]);
 
+/* ---- Fields without any device allocation --------------------------------
+ * No counterpart in the paper: an entry point for callers that cannot
+ * allocate device memory (code that runs inside another framework's memory
+ * pool, plugin hosts that forbid cudaMalloc, processes whose device footprint
+ * must not grow after start-up).  It computes what wdlb_fields computes for a
+ * state at rest with respect to its own history -- the smeared density nbar,
+ * C (Eq. campoc) and A (Eq. campod) with the neighbours' velocity u -- from
+ * device arrays n (N doubles) and u (3N doubles), into device arrays nbar (N,
+ * may be NULL), C (3N) and A (6N: xx, yy, zz, xy, xz, yz), FP32 arithmetic.
+ * Solid nodes (walls) report 0.
+ *
+ * Its scratch is one file-scope __device__ array of fixed size (about 5 MiB:
+ * the field arrays for WDLB_STATIC_MAX_NODES nodes, the stencil tables and a
+ * reduction slot) that every GPU which loads the library holds until the
+ * process exits; the call allocates and frees nothing.  Lattices with more
+ * than WDLB_STATIC_MAX_NODES nodes, or sigma outside [1, 8], are rejected with
+ * WDLB_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) on the current device; make that first call
+ * before any stream capture.  All work is enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream); the stencil tables are copied
+ * from pageable host memory, so the call may wait for work already queued on
+ * that stream.  Every call shares the one array and the array keeps the last
+ * call's contents: calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
+#define WDLB_STATIC_MAX_NODES 262144
+wdlb_status wdlb_fields_static(wdlb_lattice lat, double sigma, int32_t walls, int32_t closure,
+                               const double *d_n, const double *d_u, double *d_nbar, double *d_C,
+                               double *d_A, void *stream);
+
 /* Number of kernels this context has launched so far (a graph replay counts
  * the kernels it contains). */
 int64_t wdlb_launch_count(const wdlb_ctx *ctx);

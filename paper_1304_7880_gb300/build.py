@@ -26,6 +26,7 @@ UNITS = [
     ("wdlb_launch_f64.o", "wdlb_launch.cu", ["-DWDLB_STORAGE=0"]),
     ("wdlb_launch_f32.o", "wdlb_launch.cu", ["-DWDLB_STORAGE=1"]),
     ("wdlb_launch_f16.o", "wdlb_launch.cu", ["-DWDLB_STORAGE=2"]),
+    ("wdlb_static.o", "wdlb_static.cu", []),
 ]
 
 

@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
         "wdlb_velocity_set": (I32, [P, P]),
         "wdlb_stencil": (I32, [D, I32, P, I32, P, P]),
         "wdlb_profile_step": (I32, [P, I64, P]),
+        "wdlb_fields_static": (I32, [wdlb_lattice, D, I32, I32, P, P, P, P, P, P]),
         "wdlb_launch_count": (I64, [P]),
         "wdlb_last_error": (ctypes.c_char_p, [P]),
         "wdlb_destroy": (None, [P]),
@@ -248,6 +249,22 @@ def wdlb_profile_step(ctx: Context, nsteps: int):
     ms = (ctypes.c_double * 3)()
     _check(load_library().wdlb_profile_step(ctx.handle, int(nsteps), ms), ctx)
     return tuple(ms)
+
+
+WDLB_STATIC_MAX_NODES = 262144
+
+
+def wdlb_fields_static(lattice, sigma, walls, closure, d_n, d_u, d_nbar, d_C, d_A, stream=None):
+    """Fields (nbar, C, A) of device arrays n, u without any device allocation
+    (see include/wdlb.h): torch CUDA tensors of float64, results written into
+    d_nbar (may be None), d_C, d_A; enqueued on `stream` (torch.cuda.Stream or
+    None for the legacy default stream)."""
+    lib = load_library()
+    nx, ny, nz = (int(v) for v in lattice)
+    ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(lib.wdlb_fields_static(wdlb_lattice(nx, ny, nz), float(sigma), 1 if walls else 0, CLOSURES[closure],
+                                  ptr(d_n), ptr(d_u), ptr(d_nbar), ptr(d_C), ptr(d_A), st))
 
 
 def wdlb_launch_count(ctx: Context) -> int:
