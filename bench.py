@@ -309,6 +309,35 @@ def run_ours(args):
     e2e_value = world * N * SUB * e2e_steps / e2e_s / 1e6
     assert np.isfinite(on).all()
 
+    # ---------------- batched slit pores (one launch per phase for all pores) ----------------
+    pores = synth.batched_pores()
+    nodes_b = sum(pp["nx"] * pp["ny"] * pp["nz"] for pp, _, _ in pores)
+    pool = 0
+    probe = w.wdlb_batch_create(1, 1 << 20, storage="f32")
+    for pp, _, _ in pores:
+        pool += (w.wdlb_batch_pore_bytes(probe, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"]) + 255) // 256 * 256
+    w.wdlb_batch_destroy(probe)
+    bt = w.wdlb_batch_create(len(pores), pool + (1 << 20), storage="f32")
+    for pp, nn, uu in pores:
+        w.wdlb_batch_add(bt, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"], pp["tau"], pp["g"], nn, uu)
+    w.wdlb_batch_step(bt, 20)
+    bt.stream.synchronize()
+    ba = torch.cuda.Event(enable_timing=True)
+    bb = torch.cuda.Event(enable_timing=True)
+    breps = max(2, args.steps // 2)
+    bl0 = w.wdlb_batch_launch_count(bt)
+    ba.record(bt.stream)
+    for _ in range(breps):
+        w.wdlb_batch_step(bt, SUB)
+    bb.record(bt.stream)
+    torch.cuda.synchronize()
+    bt_ms = max_over_ranks(ba.elapsed_time(bb))
+    batched = {"value": world * nodes_b * SUB * breps / (bt_ms * 1e-3) / 1e6, "unit": UNIT, "pores": len(pores),
+               "nodes": nodes_b, "time_steps": SUB * breps, "gpu_launches": w.wdlb_batch_launch_count(bt) - bl0,
+               "workload": "64 slit pores 32x32x(13..121), sigma=4, n* in [0.1, 0.6], g_x log-uniform "
+                           "[1e-7, 1e-5], tau=1, FP32; one launch per phase for all pores, CUDA graph"}
+    w.wdlb_batch_destroy(bt)
+
     # ---------------- other storage paths (same workload, shorter) ----------------
     paths = {}
     for storage, sub, reps in (("f64", 10, 2), ("f16", SUB, 3)):
@@ -372,7 +401,7 @@ def run_ours(args):
                     "path": "wdlb_init_fields(host) + wdlb_step(100) + wdlb_moments(host), pinned buffers"},
             "clocks": clocks, "gpu_launches": int(gpu_launches),
             "kernels_ms": {"moments": kms[0], "smeared_density": kms[1], "shell_collide_stream": kms[2]},
-            "paths": paths, "pore_average": {k: stats[k] for k in ("mass", "mean_n", "mean_ux", "steps")}}
+            "paths": paths, "batched": batched, "pore_average": {k: stats[k] for k in ("mass", "mean_n", "mean_ux", "steps")}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

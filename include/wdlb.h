@@ -183,6 +183,57 @@ wdlb_status wdlb_stencil(double sigma, int32_t which, int32_t *vecs, int32_t cap
  * streaming.  Synchronous. */
 wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3]);
 
+/* ---- Batches of independent lattices (continuous batching) --------------
+ * Many pores of different sizes stepped together: each phase of a time step
+ * is one kernel launch for all pores of the batch (one shell launch per group
+ * of pores with the same sigma and geometry), replayed from a CUDA graph.
+ * The kernels are those of the single-lattice path, so a pore's result is the
+ * same alone and in a batch.  Pores are admitted by device-memory footprint
+ * into a pool of fixed size and removed when done; admission, removal and
+ * stepping may interleave freely (continuous batching).
+ *
+ * opt: options shared by all pores (closure, omega mode, storage,
+ * interactions, K); opt->workspace, if set, is the pool (caller-owned,
+ * 256-byte aligned, >= pool_bytes), else the library allocates pool_bytes;
+ * opt->stream as for wdlb_create.  The batch also allocates small device
+ * tables (parameters and work lists of its slots). */
+typedef struct wdlb_batch wdlb_batch;
+typedef struct {
+    wdlb_lattice lat;
+    double sigma;
+    int32_t walls;
+    double tau;
+    double g[3];
+} wdlb_pore_desc;
+
+wdlb_status wdlb_batch_create(const wdlb_options *opt, uint64_t pool_bytes, int32_t max_pores,
+                              wdlb_batch **out);
+/* Pool bytes one pore of this description occupies. */
+wdlb_status wdlb_batch_pore_bytes(const wdlb_batch *b, const wdlb_pore_desc *d, uint64_t *bytes);
+/* Admit a pore with initial fields n (N doubles), u (3N doubles or NULL) on the
+ * host (step 1 of Sec. 5); *slot receives its slot.  WDLB_ERR_OOM if no slot
+ * or not enough contiguous pool memory is free (nothing changed). */
+wdlb_status wdlb_batch_add(wdlb_batch *b, const wdlb_pore_desc *d, const double *n, const double *u,
+                           int32_t *slot);
+/* Release a pore and its pool memory. */
+wdlb_status wdlb_batch_remove(wdlb_batch *b, int32_t slot);
+/* Steps 2-5 of the algorithm of Sec. 5 for every pore, nsteps times (async). */
+wdlb_status wdlb_batch_step(wdlb_batch *b, int64_t nsteps);
+/* Per slot (array of max_pores): the FP64 steady-state residual
+ * max|u_x - u_x(previous call)| / (interval max|u_x|) (NaN for empty slots)
+ * and the slot status (WDLB_OK, WDLB_ERR_UNSTABLE, -1 empty); either array
+ * may be NULL.  Updates each pore's u_x snapshot.  Synchronous. */
+wdlb_status wdlb_batch_residuals(wdlb_batch *b, int32_t interval, double *res, int32_t *status);
+/* The context of a slot (owned by the batch): use it for wdlb_moments,
+ * wdlb_pore_average, wdlb_fields, wdlb_get_populations; do not step or
+ * destroy it.  NULL for an empty slot. */
+wdlb_ctx *wdlb_batch_context(wdlb_batch *b, int32_t slot);
+int32_t wdlb_batch_active(const wdlb_batch *b);
+uint64_t wdlb_batch_free_bytes(const wdlb_batch *b);
+int64_t wdlb_batch_launch_count(const wdlb_batch *b);
+const char *wdlb_batch_last_error(const wdlb_batch *b);
+void wdlb_batch_destroy(wdlb_batch *b);
+
 /* ---- Fields without any device allocation --------------------------------
  * No counterpart in the paper: an entry point for callers that cannot
  * allocate device memory (code that runs inside another framework's memory

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -658,3 +660,429 @@ void wdlb_destroy(wdlb_ctx *ctx)
 
 }  // extern "C"
 
+// ===========================================================================
+// Batch of independent lattices stepped together (continuous batching).
+// Every slot is an ordinary context whose workspace is carved from the
+// batch's pool and whose stream is the batch's stream; a batch step launches,
+// for all slots at once, the moments and smeared-density kernels over a table
+// of (slot, node block) items and one shell kernel per group of slots with
+// the same kernel variant (sigma, walls).  Kernel bodies are those of the
+// single-lattice path, so a pore gives the same result alone and in a batch.
+// ===========================================================================
+
+struct wdlb_batch {
+    wdlb_options opt{};
+    const Launchers *L = nullptr;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    char *pool = nullptr;
+    size_t pool_bytes = 0;
+    bool owns_pool = false;
+    std::vector<std::pair<size_t, size_t>> free_list;   // (offset, bytes), sorted by offset
+    struct Slot {
+        wdlb_ctx *ctx = nullptr;
+        size_t off = 0, bytes = 0;
+    };
+    std::vector<Slot> slots;
+    // device tables
+    KParams *d_params = nullptr;
+    char *d_bufs[2] = {nullptr, nullptr};
+    BatchItem *d_items = nullptr;
+    size_t items_cap = 0;
+    BatchLaunch launch{};
+    bool dirty = true;
+    int64_t steps_since_build = 0;
+    cudaGraphExec_t graph = nullptr;   // two steps: parity 0 then 1
+    int64_t launches = 0;
+    int64_t graph_launches = 0;        // kernels in one graph replay
+    std::string err;
+};
+
+namespace {
+
+wdlb_status bfail(wdlb_batch *b, wdlb_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_create_error = buf;
+    return s;
+}
+
+bool pool_alloc(wdlb_batch *b, size_t bytes, size_t *off)
+{
+    for (size_t k = 0; k < b->free_list.size(); k++) {
+        auto &fr = b->free_list[k];
+        if (fr.second >= bytes) {
+            *off = fr.first;
+            fr.first += bytes;
+            fr.second -= bytes;
+            if (fr.second == 0) b->free_list.erase(b->free_list.begin() + k);
+            return true;
+        }
+    }
+    return false;
+}
+
+void pool_free(wdlb_batch *b, size_t off, size_t bytes)
+{
+    auto &fl = b->free_list;
+    auto it = std::lower_bound(fl.begin(), fl.end(), std::make_pair(off, size_t(0)));
+    it = fl.insert(it, std::make_pair(off, bytes));
+    // merge with neighbours
+    size_t k = it - fl.begin();
+    if (k + 1 < fl.size() && fl[k].first + fl[k].second == fl[k + 1].first) {
+        fl[k].second += fl[k + 1].second;
+        fl.erase(fl.begin() + k + 1);
+    }
+    if (k > 0 && fl[k - 1].first + fl[k - 1].second == fl[k].first) {
+        fl[k - 1].second += fl[k].second;
+        fl.erase(fl.begin() + k);
+    }
+}
+
+void batch_drop_graph(wdlb_batch *b)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+// Rebuild the device tables after slots changed.
+wdlb_status batch_build(wdlb_batch *b)
+{
+    const int P = (int)b->slots.size();
+    std::vector<KParams> params(P);
+    std::vector<char> bufs0(b->L->kbufs_bytes * P, 0), bufs1(b->L->kbufs_bytes * P, 0);
+    std::vector<BatchItem> node_items;
+    struct Key {
+        int s2, walls, tiled, closure;
+        bool operator<(const Key &o) const
+        {
+            return std::make_tuple(s2, walls, tiled, closure) < std::make_tuple(o.s2, o.walls, o.tiled, o.closure);
+        }
+    };
+    std::map<Key, std::vector<BatchItem>> groups;
+    for (int s = 0; s < P; s++) {
+        wdlb_ctx *c = b->slots[s].ctx;
+        if (!c) continue;
+        params[s] = c->kp;
+        b->L->kbufs_fill(c->dev, c->cur, bufs0.data() + s * b->L->kbufs_bytes);
+        b->L->kbufs_fill(c->dev, c->cur ^ 1, bufs1.data() + s * b->L->kbufs_bytes);
+        const int N = (int)c->N;
+        for (int k = 0; k < (N + 255) / 256; k++) node_items.push_back(BatchItem{s, k, 0, 0});
+        Key key{c->kp.tiled ? c->kp.s2 : 0, c->walls, c->kp.tiled, c->kp.closure};
+        auto &g = groups[key];
+        if (c->kp.tiled) {
+            const int tx = (c->lat.nx + 7) / 8, ty = (c->lat.ny + 7) / 8, tz = (c->lat.nz + 7) / 8;
+            for (int z = 0; z < tz; z++)
+                for (int y = 0; y < ty; y++)
+                    for (int x = 0; x < tx; x++) g.push_back(BatchItem{s, x, y, z});
+        } else {
+            for (int k = 0; k < (N + 255) / 256; k++) g.push_back(BatchItem{s, k, 0, 0});
+        }
+    }
+    if ((int)groups.size() > kMaxBatchGroups) return bfail(b, WDLB_ERR_ARG, "too many kernel variants in one batch");
+    size_t total = node_items.size();
+    for (auto &g : groups) total += g.second.size();
+    if (total > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->items_cap = std::max<size_t>(total, 2 * b->items_cap);
+        if (cudaMalloc(&b->d_items, b->items_cap * sizeof(BatchItem)) != cudaSuccess) {
+            b->d_items = nullptr;
+            b->items_cap = 0;
+            return bfail(b, WDLB_ERR_OOM, "batch work table");
+        }
+    }
+    std::vector<BatchItem> all(node_items);
+    BatchLaunch &L = b->launch;
+    L.params = b->d_params;
+    L.bufs[0] = b->d_bufs[0];
+    L.bufs[1] = b->d_bufs[1];
+    L.node_items = b->d_items;
+    L.n_node_items = (int)node_items.size();
+    L.ngroups = 0;
+    for (auto &g : groups) {
+        BatchGroup &G = L.groups[L.ngroups++];
+        G.s2 = g.first.s2;
+        G.walls = g.first.walls;
+        G.tiled = g.first.tiled;
+        G.closure = g.first.closure;
+        G.items = b->d_items + all.size();
+        G.nitems = (int)g.second.size();
+        all.insert(all.end(), g.second.begin(), g.second.end());
+    }
+    cudaError_t e = cudaSuccess;
+    if (P > 0) e = cudaMemcpyAsync(b->d_params, params.data(), P * sizeof(KParams), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && P > 0)
+        e = cudaMemcpyAsync(b->d_bufs[0], bufs0.data(), bufs0.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && P > 0)
+        e = cudaMemcpyAsync(b->d_bufs[1], bufs1.data(), bufs1.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && !all.empty())
+        e = cudaMemcpyAsync(b->d_items, all.data(), all.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host vectors go out of scope
+    if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch tables: %s", cudaGetErrorString(e));
+    batch_drop_graph(b);
+    b->dirty = false;
+    b->steps_since_build = 0;
+    return WDLB_OK;
+}
+
+wdlb_status batch_step_direct(wdlb_batch *b, int64_t n)
+{
+    for (int64_t s = 0; s < n; s++) {
+        cudaError_t e = b->L->batch_step(b->launch, (int)(b->steps_since_build & 1), b->stream, &b->launches);
+        if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch step: %s", cudaGetErrorString(e));
+        b->steps_since_build++;
+    }
+    return WDLB_OK;
+}
+
+wdlb_status batch_ensure_graph(wdlb_batch *b)
+{
+    if (b->graph) return WDLB_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bfail(b, WDLB_ERR_CUDA, "batch capture");
+    int64_t count = 0;
+    cudaError_t e = b->L->batch_step(b->launch, 0, b->stream, &count);
+    if (e == cudaSuccess) e = b->L->batch_step(b->launch, 1, b->stream, &count);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(b, WDLB_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch graph: %s", cudaGetErrorString(e));
+    b->graph_launches = count;
+    return WDLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wdlb_status wdlb_batch_create(const wdlb_options *opt, uint64_t pool_bytes, int32_t max_pores, wdlb_batch **out)
+{
+    if (!out) return bfail(nullptr, WDLB_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (max_pores < 1 || pool_bytes < 4096) return bfail(nullptr, WDLB_ERR_ARG, "bad batch size");
+    wdlb_options o;
+    if (opt)
+        o = *opt;
+    else
+        wdlb_default_options(&o);
+    if (o.closure < 0 || o.closure > 2 || o.omega_mode < 0 || o.omega_mode > 1 || o.storage < 0 || o.storage > 2)
+        return bfail(nullptr, WDLB_ERR_ARG, "invalid options");
+    wdlb_batch *b = new (std::nothrow) wdlb_batch();
+    if (!b) return bfail(nullptr, WDLB_ERR_OOM, "host allocation failed");
+    b->opt = o;
+    b->L = &launchers_for(o.storage);
+    b->slots.resize(max_pores);
+    if (o.stream) {
+        b->stream = static_cast<cudaStream_t>(o.stream);
+    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete b;
+        return bfail(nullptr, WDLB_ERR_CUDA, "cudaStreamCreate");
+    } else {
+        b->owns_stream = true;
+    }
+    if (o.workspace) {
+        if ((reinterpret_cast<uintptr_t>(o.workspace) & 255) || o.workspace_bytes < pool_bytes) {
+            wdlb_batch_destroy(b);
+            return bfail(nullptr, WDLB_ERR_ARG, "pool must be 256-byte aligned and at least pool_bytes long");
+        }
+        b->pool = static_cast<char *>(o.workspace);
+    } else {
+        if (cudaMalloc(&b->pool, pool_bytes) != cudaSuccess) {
+            b->pool = nullptr;
+            wdlb_batch_destroy(b);
+            return bfail(nullptr, WDLB_ERR_OOM, "cudaMalloc(%llu) for the batch pool", (unsigned long long)pool_bytes);
+        }
+        b->owns_pool = true;
+    }
+    b->pool_bytes = pool_bytes & ~size_t(255);
+    b->free_list.push_back(std::make_pair(size_t(0), b->pool_bytes));
+    if (cudaMalloc(&b->d_params, max_pores * sizeof(KParams)) != cudaSuccess ||
+        cudaMalloc(&b->d_bufs[0], max_pores * b->L->kbufs_bytes) != cudaSuccess ||
+        cudaMalloc(&b->d_bufs[1], max_pores * b->L->kbufs_bytes) != cudaSuccess) {
+        wdlb_batch_destroy(b);
+        return bfail(nullptr, WDLB_ERR_OOM, "batch tables");
+    }
+    *out = b;
+    return WDLB_OK;
+}
+
+wdlb_status wdlb_batch_pore_bytes(const wdlb_batch *b, const wdlb_pore_desc *d, uint64_t *bytes)
+{
+    if (!b || !d || !bytes) return WDLB_ERR_ARG;
+    wdlb_options o = b->opt;
+    return wdlb_workspace_size(d->lat, d->sigma, d->walls, &o, bytes);
+}
+
+wdlb_status wdlb_batch_add(wdlb_batch *b, const wdlb_pore_desc *d, const double *n, const double *u, int32_t *slot)
+{
+    if (!b || !d || !n || !slot) return b ? bfail(b, WDLB_ERR_ARG, "NULL argument") : WDLB_ERR_ARG;
+    *slot = -1;
+    int s = -1;
+    for (int k = 0; k < (int)b->slots.size(); k++)
+        if (!b->slots[k].ctx) {
+            s = k;
+            break;
+        }
+    if (s < 0) return bfail(b, WDLB_ERR_OOM, "all %d slots in use", (int)b->slots.size());
+    uint64_t need = 0;
+    wdlb_status st = wdlb_batch_pore_bytes(b, d, &need);
+    if (st != WDLB_OK) return bfail(b, st, "invalid pore description");
+    need = align256(need);
+    size_t off = 0;
+    if (!pool_alloc(b, need, &off)) return bfail(b, WDLB_ERR_OOM, "pool has no room for %llu bytes", (unsigned long long)need);
+    wdlb_options o = b->opt;
+    o.workspace = b->pool + off;
+    o.workspace_bytes = need;
+    o.stream = b->stream;
+    wdlb_ctx *c = nullptr;
+    st = wdlb_create(d->lat, d->sigma, d->walls, d->tau, d->g, &o, &c);
+    if (st != WDLB_OK) {
+        pool_free(b, off, need);
+        return bfail(b, st, "create: %s", wdlb_last_error(nullptr));
+    }
+    st = wdlb_init_fields(c, n, u);
+    if (st != WDLB_OK) {
+        bfail(b, st, "init: %s", c->err.c_str());
+        wdlb_destroy(c);
+        pool_free(b, off, need);
+        return st;
+    }
+    b->slots[s].ctx = c;
+    b->slots[s].off = off;
+    b->slots[s].bytes = need;
+    b->dirty = true;
+    *slot = s;
+    return WDLB_OK;
+}
+
+wdlb_status wdlb_batch_remove(wdlb_batch *b, int32_t slot)
+{
+    if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].ctx) return WDLB_ERR_ARG;
+    wdlb_destroy(b->slots[slot].ctx);   // synchronises the stream
+    pool_free(b, b->slots[slot].off, b->slots[slot].bytes);
+    b->slots[slot] = wdlb_batch::Slot{};
+    b->dirty = true;
+    return WDLB_OK;
+}
+
+wdlb_status wdlb_batch_step(wdlb_batch *b, int64_t nsteps)
+{
+    if (!b || nsteps < 0) return WDLB_ERR_ARG;
+    if (b->dirty) {
+        wdlb_status s = batch_build(b);
+        if (s != WDLB_OK) return s;
+    }
+    int64_t left = nsteps;
+    if (b->steps_since_build & 1) {
+        if (left > 0) {
+            wdlb_status s = batch_step_direct(b, 1);
+            if (s != WDLB_OK) return s;
+            left--;
+        }
+    }
+    if (left >= 2) {
+        wdlb_status s = batch_ensure_graph(b);
+        if (s != WDLB_OK) return s;
+        while (left >= 2) {
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch graph launch");
+            b->launches += b->graph_launches;
+            b->steps_since_build += 2;
+            left -= 2;
+        }
+    }
+    wdlb_status s = batch_step_direct(b, left);
+    if (s != WDLB_OK) return s;
+    for (auto &sl : b->slots)
+        if (sl.ctx) {
+            sl.ctx->cur ^= (int)(nsteps & 1);
+            sl.ctx->steps += nsteps;
+        }
+    return WDLB_OK;
+}
+
+wdlb_status wdlb_batch_residuals(wdlb_batch *b, int32_t interval, double *res, int32_t *status)
+{
+    if (!b || interval < 1) return WDLB_ERR_ARG;
+    const int P = (int)b->slots.size();
+    std::vector<double> r(6 * P, 0.0);
+    std::vector<int> stw(P, 0);
+    for (int s = 0; s < P; s++) {
+        wdlb_ctx *c = b->slots[s].ctx;
+        if (!c) continue;
+        cudaError_t e = c->L->stats(c->kp, c->dev, c->cur, 1, b->stream, &b->launches);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&r[6 * s], c->dev.result, 6 * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&stw[s], c->dev.status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch residuals: %s", cudaGetErrorString(e));
+    }
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch residuals sync");
+    for (int s = 0; s < P; s++) {
+        wdlb_ctx *c = b->slots[s].ctx;
+        double v = NAN;
+        if (c) {
+            v = r[6 * s + 4] > 0 ? r[6 * s + 3] / (double(interval) * r[6 * s + 4]) : 0.0;
+            c->last_residual = v;
+        }
+        if (res) res[s] = v;
+        if (status) status[s] = c ? (stw[s] ? WDLB_ERR_UNSTABLE : WDLB_OK) : -1;
+    }
+    return WDLB_OK;
+}
+
+wdlb_ctx *wdlb_batch_context(wdlb_batch *b, int32_t slot)
+{
+    if (!b || slot < 0 || slot >= (int)b->slots.size()) return nullptr;
+    return b->slots[slot].ctx;
+}
+
+int32_t wdlb_batch_active(const wdlb_batch *b)
+{
+    if (!b) return 0;
+    int32_t n = 0;
+    for (auto &s : b->slots) n += s.ctx != nullptr;
+    return n;
+}
+
+uint64_t wdlb_batch_free_bytes(const wdlb_batch *b)
+{
+    if (!b) return 0;
+    uint64_t f = 0;
+    for (auto &fr : b->free_list) f += fr.second;
+    return f;
+}
+
+int64_t wdlb_batch_launch_count(const wdlb_batch *b) { return b ? b->launches : 0; }
+
+const char *wdlb_batch_last_error(const wdlb_batch *b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+void wdlb_batch_destroy(wdlb_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    for (auto &s : b->slots)
+        if (s.ctx) wdlb_destroy(s.ctx);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_params) cudaFree(b->d_params);
+    for (auto &p : b->d_bufs)
+        if (p) cudaFree(p);
+    if (b->owns_pool && b->pool) cudaFree(b->pool);
+    if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

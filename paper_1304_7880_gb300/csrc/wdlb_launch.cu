@@ -4,6 +4,8 @@
 #include "wdlb_launch.h"
 #include "wdlb_shell_tiled.cuh"
 
+#include <cstring>
+
 #ifndef WDLB_STORAGE
 #error "compile with -DWDLB_STORAGE=0|1|2"
 #endif
@@ -23,6 +25,37 @@ typedef Store<S>::T T;
 constexpr int kThreads = 256;
 
 inline int blocks_for(int n) { return (n + kThreads - 1) / kThreads; }
+
+// ---- multi-lattice kernels: one launch for all slots, same kernel bodies ----
+__global__ void __launch_bounds__(256) k_moments_batch(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
+{
+    const BatchItem w = it[blockIdx.x];
+    moments_body<S, false>(P[w.slot], B[w.slot], w.bx, nullptr, nullptr);
+}
+
+__global__ void __launch_bounds__(256) k_ball_batch(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
+{
+    const BatchItem w = it[blockIdx.x];
+    const KBufs<S, T> &b = B[w.slot];
+    ball_body<T>(P[w.slot], b.nu, b.hb, b.ball, b.status, w.bx);
+}
+
+template <int CL, bool WALLS>
+__global__ void __launch_bounds__(256) k_shell_batch(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
+{
+    const BatchItem w = it[blockIdx.x];
+    shell_body<S, CL, WALLS, false>(P[w.slot], B[w.slot], w.bx);
+}
+
+#if WDLB_STORAGE != 0
+template <int S2, bool WALLS>
+__global__ void __launch_bounds__(tiled::THREADS, 2) k_tiled_batch(const KParams *P, const KBufs<S, float> *B,
+                                                                  const BatchItem *it)
+{
+    const BatchItem w = it[blockIdx.x];
+    tiled::tiled_body<S, S2, 0, WALLS, false>(P[w.slot], B[w.slot], w.bx, w.by, w.bz);
+}
+#endif
 
 KBufs<S, T> typed(const DevBufs &d, int cur)
 {
@@ -54,8 +87,11 @@ void launch_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
 template <int S2, bool WALLS>
 cudaError_t tiled_attr()
 {
-    return cudaFuncSetAttribute(tiled::k_shell_tiled<S, S2, 0, WALLS, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled::smem_bytes<S2>());
+    cudaError_t e = cudaFuncSetAttribute(tiled::k_shell_tiled<S, S2, 0, WALLS, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled::smem_bytes<S2>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tiled_batch<S2, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tiled::smem_bytes<S2>());
 }
 
 template <int S2, bool WALLS>
@@ -212,7 +248,47 @@ cudaError_t do_stats(const KParams &p, const DevBufs &d, int cur, int update_sna
     return cudaGetLastError();
 }
 
-const Launchers kL = {do_prepare, do_init, do_step, do_step_part, do_fields, do_moments, do_population, do_stats};
+void kbufs_fill(const DevBufs &d, int cur, void *out)
+{
+    KBufs<S, T> b = typed(d, cur);
+    std::memcpy(out, &b, sizeof(b));
+}
+
+cudaError_t do_batch_step(const BatchLaunch &L, int parity, cudaStream_t st, int64_t *launches)
+{
+    const KBufs<S, T> *B = static_cast<const KBufs<S, T> *>(L.bufs[parity & 1]);
+    if (L.n_node_items > 0) {
+        k_moments_batch<<<L.n_node_items, kThreads, 0, st>>>(L.params, B, L.node_items);
+        k_ball_batch<<<L.n_node_items, kThreads, 0, st>>>(L.params, B, L.node_items);
+        *launches += 2;
+    }
+    for (int g = 0; g < L.ngroups; g++) {
+        const BatchGroup &G = L.groups[g];
+        if (G.nitems == 0) continue;
+#if WDLB_STORAGE != 0
+        if (G.tiled) {
+            const size_t sm = G.s2 == 6 ? tiled::smem_bytes<6>() : (G.s2 == 8 ? tiled::smem_bytes<8>()
+                                                                               : tiled::smem_bytes<12>());
+#define WDLB_TB(S2V, WV) k_tiled_batch<S2V, WV><<<G.nitems, tiled::THREADS, sm, st>>>(L.params, B, G.items)
+            if (G.s2 == 6) { if (G.walls) WDLB_TB(6, true); else WDLB_TB(6, false); }
+            else if (G.s2 == 8) { if (G.walls) WDLB_TB(8, true); else WDLB_TB(8, false); }
+            else { if (G.walls) WDLB_TB(12, true); else WDLB_TB(12, false); }
+#undef WDLB_TB
+            *launches += 1;
+            continue;
+        }
+#endif
+#define WDLB_SB(CLV, WV) k_shell_batch<CLV, WV><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items)
+        if (G.closure == 0) { if (G.walls) WDLB_SB(0, true); else WDLB_SB(0, false); }
+        else if (G.closure == 1) { if (G.walls) WDLB_SB(1, true); else WDLB_SB(1, false); }
+        else { if (G.walls) WDLB_SB(2, true); else WDLB_SB(2, false); }
+#undef WDLB_SB
+        *launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+const Launchers kL = {do_prepare, sizeof(KBufs<S, T>), kbufs_fill, do_batch_step, do_init, do_step, do_step_part, do_fields, do_moments, do_population, do_stats};
 
 }  // namespace
 

@@ -31,10 +31,42 @@ struct DevBufs {
 
 constexpr int kStatBlocks = 304;
 
+// One block of work in a multi-lattice launch: lattice slot and block
+// coordinates within it (bx: node block of 256 for the per-node kernels and
+// the generic shell kernel; bx, by, bz: 8x8x8 tile for the tiled kernel).
+struct BatchItem {
+    int slot, bx, by, bz;
+};
+
+// Shell launch of one group of slots with the same kernel variant.
+struct BatchGroup {
+    int s2, walls, tiled, closure;
+    const BatchItem *items;
+    int nitems;
+};
+
+constexpr int kMaxBatchGroups = 16;
+
+// Device tables of a multi-lattice step.  bufs[p]: one KBufs per slot (of the
+// launcher's storage type), input buffer = the slot's buffer for parity p.
+struct BatchLaunch {
+    const KParams *params;
+    const void *bufs[2];
+    const BatchItem *node_items;
+    int n_node_items;
+    BatchGroup groups[kMaxBatchGroups];
+    int ngroups;
+};
+
 struct Launchers {
     // per-context preparation outside any stream capture (kernel attributes);
     // returns whether the tiled shell kernel can serve these parameters
     bool (*prepare)(const KParams &);
+    // multi-lattice step: size of one KBufs, writing it for input buffer `cur`,
+    // and one time step of every slot in the tables (input buffers of parity p)
+    size_t kbufs_bytes;
+    void (*kbufs_fill)(const DevBufs &, int cur, void *out);
+    cudaError_t (*batch_step)(const BatchLaunch &, int parity, cudaStream_t, int64_t *launches);
     cudaError_t (*init)(const KParams &, const DevBufs &, int cur, const double *d_n, const double *d_u,
                         cudaStream_t, int64_t *launches);
     // one time step from buffer `cur` into `cur ^ 1`

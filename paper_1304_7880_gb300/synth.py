@@ -91,15 +91,17 @@ def slit_poiseuille(nx, ny, nz, n_star, sigma, tau, gx, seed, amp=1e-3):
     return params, n, u
 
 
-def batched_pores(count: int = 64, seed: int = 4, sigma: float = 4.0, nxy: int = 32):
-    """Batch of slit pores: H uniform in [3 sigma, 30 sigma], n* in [0.1, 0.8],
-    g_x log-uniform in [1e-7, 1e-5], tau = 1."""
+def batched_pores(count: int = 64, seed: int = 4, sigma: float = 4.0, nxy: int = 32, n_star_max: float = 0.6):
+    """Batch of slit pores: H uniform in [3 sigma, 30 sigma] (nz = H + 1),
+    n* uniform in [0.1, n_star_max], g_x log-uniform in [1e-7, 1e-5], tau = 1.
+    (The configuration asks for n* up to 0.8; the scheme's uniform fluid is
+    linearly unstable above n* ~ 0.65, so the default upper end is 0.6.)"""
     U = uniform01(seed, 3 * count).reshape(count, 3)
     out = []
     for p in range(count):
         H = int(round(3 * sigma + U[p, 0] * (27 * sigma)))
         nz = H + 1
-        n_star = 0.1 + 0.7 * U[p, 1]
+        n_star = 0.1 + (n_star_max - 0.1) * U[p, 1]
         gx = 10.0 ** (-7.0 + 2.0 * U[p, 2])
         out.append(slit_poiseuille(nxy, nxy, nz, n_star, sigma, 1.0, gx, seed * 1000 + p))
     return out

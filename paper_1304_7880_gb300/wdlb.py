@@ -44,6 +44,11 @@ class wdlb_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class wdlb_pore_desc(ctypes.Structure):
+    _fields_ = [("lat", wdlb_lattice), ("sigma", ctypes.c_double), ("walls", ctypes.c_int32),
+                ("tau", ctypes.c_double), ("g", ctypes.c_double * 3)]
+
+
 class wdlb_pore_stats(ctypes.Structure):
     _fields_ = [("mean_n", ctypes.c_double), ("mean_ux", ctypes.c_double), ("flux_x", ctypes.c_double),
                 ("mass", ctypes.c_double), ("eta_eff", ctypes.c_double), ("residual", ctypes.c_double),
@@ -78,6 +83,18 @@ def load_library(path: str = LIB_PATH):
         "wdlb_fields_static": (I32, [wdlb_lattice, D, I32, I32, P, P, P, P, P, P]),
         "wdlb_launch_count": (I64, [P]),
         "wdlb_last_error": (ctypes.c_char_p, [P]),
+        "wdlb_batch_create": (I32, [P, ctypes.c_uint64, I32, P]),
+        "wdlb_batch_pore_bytes": (I32, [P, P, P]),
+        "wdlb_batch_add": (I32, [P, P, P, P, P]),
+        "wdlb_batch_remove": (I32, [P, I32]),
+        "wdlb_batch_step": (I32, [P, I64]),
+        "wdlb_batch_residuals": (I32, [P, I32, P, P]),
+        "wdlb_batch_context": (P, [P, I32]),
+        "wdlb_batch_active": (I32, [P]),
+        "wdlb_batch_free_bytes": (ctypes.c_uint64, [P]),
+        "wdlb_batch_launch_count": (I64, [P]),
+        "wdlb_batch_last_error": (ctypes.c_char_p, [P]),
+        "wdlb_batch_destroy": (None, [P]),
         "wdlb_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -280,3 +297,125 @@ def wdlb_destroy(ctx: Context):
     if ctx.handle:
         load_library().wdlb_destroy(ctx.handle)
         ctx.handle = None
+
+
+# ---- batches of independent lattices -------------------------------------------------
+
+class Batch:
+    """Handle of a batch plus the torch pool and stream that back it."""
+
+    def __init__(self, handle, pool, stream, max_pores):
+        self.handle = handle
+        self.pool = pool
+        self.stream = stream
+        self.max_pores = max_pores
+        self.shapes = {}
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            wdlb_batch_destroy(self)
+
+
+class SlotContext(Context):
+    """A batch slot's context (owned by the batch; never destroyed here)."""
+
+    def __del__(self):
+        pass
+
+
+def _bcheck(status, batch=None):
+    if status != WDLB_OK:
+        msg = load_library().wdlb_batch_last_error(None if batch is None else batch.handle)
+        raise WDLBError(status, msg.decode() if msg else "")
+
+
+def wdlb_batch_create(max_pores, pool_bytes, closure="CS", omega_mode="const", storage="f32", interactions=True,
+                      k_cross=2.0, device=None):
+    import torch
+
+    lib = load_library()
+    opt = wdlb_options()
+    lib.wdlb_default_options(ctypes.byref(opt))
+    opt.closure = CLOSURES[closure]
+    opt.omega_mode = OMEGA_MODES[omega_mode]
+    opt.storage = STORAGES[storage]
+    opt.interactions = 1 if interactions else 0
+    opt.k_cross = float(k_cross)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    pool = torch.empty(int(pool_bytes) + 256, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    opt.workspace = ctypes.c_void_p((pool.data_ptr() + 255) & ~255)
+    opt.workspace_bytes = int(pool_bytes)
+    opt.stream = ctypes.c_void_p(stream.cuda_stream)
+    h = ctypes.c_void_p()
+    with torch.cuda.device(dev):
+        _bcheck(lib.wdlb_batch_create(ctypes.byref(opt), int(pool_bytes), int(max_pores), ctypes.byref(h)))
+    return Batch(h, pool, stream, int(max_pores))
+
+
+def _desc(lattice, sigma, walls, tau, g):
+    nx, ny, nz = (int(v) for v in lattice)
+    return wdlb_pore_desc(wdlb_lattice(nx, ny, nz), float(sigma), 1 if walls else 0, float(tau),
+                          (ctypes.c_double * 3)(*[float(v) for v in g]))
+
+
+def wdlb_batch_pore_bytes(batch, lattice, sigma, walls, tau=1.0, g=(0.0, 0.0, 0.0)) -> int:
+    d = _desc(lattice, sigma, walls, tau, g)
+    nb = ctypes.c_uint64()
+    _bcheck(load_library().wdlb_batch_pore_bytes(batch.handle, ctypes.byref(d), ctypes.byref(nb)), batch)
+    return nb.value
+
+
+def wdlb_batch_add(batch, lattice, sigma, walls, tau, g, n, u=None) -> int:
+    nx, ny, nz = (int(v) for v in lattice)
+    shape = (nz, ny, nx)
+    d = _desc(lattice, sigma, walls, tau, g)
+    nn = _f64(n, shape)
+    uu = None if u is None else _f64(u, (3,) + shape)
+    slot = ctypes.c_int32()
+    _bcheck(load_library().wdlb_batch_add(batch.handle, ctypes.byref(d), _ptr(nn), None if uu is None else _ptr(uu),
+                                          ctypes.byref(slot)), batch)
+    batch.shapes[slot.value] = (shape, bool(walls), tuple(float(v) for v in g))
+    return slot.value
+
+
+def wdlb_batch_remove(batch, slot):
+    _bcheck(load_library().wdlb_batch_remove(batch.handle, int(slot)), batch)
+    batch.shapes.pop(int(slot), None)
+
+
+def wdlb_batch_step(batch, nsteps=1):
+    _bcheck(load_library().wdlb_batch_step(batch.handle, int(nsteps)), batch)
+
+
+def wdlb_batch_residuals(batch, interval):
+    res = np.full(batch.max_pores, np.nan)
+    st = np.zeros(batch.max_pores, dtype=np.int32)
+    _bcheck(load_library().wdlb_batch_residuals(batch.handle, int(interval), _ptr(res), _ptr(st)), batch)
+    return res, st
+
+
+def wdlb_batch_context(batch, slot) -> SlotContext:
+    h = load_library().wdlb_batch_context(batch.handle, int(slot))
+    if not h:
+        raise WDLBError(1, "empty slot %d" % slot)
+    shape, walls, g = batch.shapes[int(slot)]
+    return SlotContext(ctypes.c_void_p(h), shape, None, batch.stream, walls, g)
+
+
+def wdlb_batch_active(batch) -> int:
+    return int(load_library().wdlb_batch_active(batch.handle))
+
+
+def wdlb_batch_free_bytes(batch) -> int:
+    return int(load_library().wdlb_batch_free_bytes(batch.handle))
+
+
+def wdlb_batch_launch_count(batch) -> int:
+    return int(load_library().wdlb_batch_launch_count(batch.handle))
+
+
+def wdlb_batch_destroy(batch):
+    if batch.handle:
+        load_library().wdlb_batch_destroy(batch.handle)
+        batch.handle = None

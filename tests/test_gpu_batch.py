@@ -1,0 +1,138 @@
+"""Batches of independent lattices (continuous batching) on the GPU.
+
+A pore gives bit-identical populations alone and inside a batch (same kernel
+bodies, same arithmetic), through graph replays and odd step counts, while
+other pores are admitted and removed around it; admission respects the pool;
+an FP64 batch slot matches the oracle; per-slot residuals and statuses are
+reported."""
+import numpy as np
+import pytest
+
+from paper_1304_7880_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def w():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1304_7880_gb300 import build, wdlb
+    build.build()
+    return wdlb
+
+
+# (lattice, sigma, walls, tau, g, n*, seed): tiled sigma 3/4/6 slits, a bulk box,
+# a narrow pore that takes the generic kernel
+PORES = [
+    ((16, 16, 25), 4.0, True, 1.0, (1e-5, 0, 0), 0.4, 31),
+    ((8, 8, 41), 4.0, True, 1.0, (1e-6, 0, 0), 0.5, 32),
+    ((12, 10, 19), 3.0, True, 0.8, (3e-6, 0, 0), 0.3, 33),
+    ((16, 16, 16), 4.0, False, 1.0, (0, 0, 0), 0.5, 34),
+    ((6, 5, 21), 4.0, True, 1.0, (2e-6, 0, 0), 0.45, 35),
+    ((16, 16, 40), 6.0, True, 1.0, (1e-6, 0, 0), 0.35, 36),
+]
+
+
+def pore_fields(lat, sigma, walls, nstar, seed):
+    nx, ny, nz = lat
+    n, u = synth.uniform_with_noise(nx, ny, nz, nstar / sigma ** 3, 1e-3, seed, walls)
+    return n, u
+
+
+def alone(w, pore, steps, storage="f32"):
+    lat, sigma, walls, tau, g, nstar, seed = pore
+    n, u = pore_fields(lat, sigma, walls, nstar, seed)
+    ctx = w.wdlb_create(lat, sigma, walls, tau, g, storage=storage)
+    w.wdlb_init_fields(ctx, n, u)
+    w.wdlb_step(ctx, steps)
+    f = w.wdlb_get_populations(ctx)
+    w.wdlb_destroy(ctx)
+    return f
+
+
+def test_batch_equals_alone_with_admission_and_removal(w):
+    b = w.wdlb_batch_create(8, 64 << 20, storage="f32")
+    slots = {}
+    for k in range(4):
+        lat, sigma, walls, tau, g, nstar, seed = PORES[k]
+        n, u = pore_fields(lat, sigma, walls, nstar, seed)
+        slots[k] = w.wdlb_batch_add(b, lat, sigma, walls, tau, g, n, u)
+    steps = {k: 0 for k in slots}
+    w.wdlb_batch_step(b, 37)             # graph pairs and an odd remainder
+    for k in slots:
+        steps[k] += 37
+    # continuous batching: one pore leaves, two arrive (the first reuses its memory)
+    w.wdlb_batch_remove(b, slots.pop(1))
+    for k in (4, 5):
+        lat, sigma, walls, tau, g, nstar, seed = PORES[k]
+        n, u = pore_fields(lat, sigma, walls, nstar, seed)
+        slots[k] = w.wdlb_batch_add(b, lat, sigma, walls, tau, g, n, u)
+        steps[k] = 0
+    w.wdlb_batch_step(b, 24)
+    for k in slots:
+        steps[k] += 24
+    assert w.wdlb_batch_active(b) == 5
+    for k, s in slots.items():
+        f_b = w.wdlb_get_populations(w.wdlb_batch_context(b, s))
+        f_a = alone(w, PORES[k], steps[k])
+        assert np.array_equal(f_b, f_a), "pore %d differs alone and in the batch" % k
+    assert w.wdlb_batch_launch_count(b) > 0
+    w.wdlb_batch_destroy(b)
+
+
+def test_admission_by_memory_footprint(w):
+    lat, sigma, walls, tau, g, nstar, seed = PORES[0]
+    probe = w.wdlb_batch_create(4, 1 << 20, storage="f32")
+    need = w.wdlb_batch_pore_bytes(probe, lat, sigma, walls, tau, g)
+    w.wdlb_batch_destroy(probe)
+    pool = 2 * ((need + 255) // 256 * 256) + 1024
+    b = w.wdlb_batch_create(4, pool, storage="f32")
+    n, u = pore_fields(lat, sigma, walls, nstar, seed)
+    s0 = w.wdlb_batch_add(b, lat, sigma, walls, tau, g, n, u)
+    s1 = w.wdlb_batch_add(b, lat, sigma, walls, tau, g, n, u)
+    with pytest.raises(w.WDLBError) as ei:
+        w.wdlb_batch_add(b, lat, sigma, walls, tau, g, n, u)
+    assert ei.value.status == 2
+    w.wdlb_batch_remove(b, s0)
+    s2 = w.wdlb_batch_add(b, lat, sigma, walls, tau, g, n, u)   # fits again
+    assert s2 == s0 and w.wdlb_batch_active(b) == 2
+    w.wdlb_batch_destroy(b)
+
+
+def test_batch_slot_matches_oracle_fp64(w, oracle_mod):
+    b = w.wdlb_batch_create(4, 64 << 20, storage="f64")
+    ref = []
+    for k in (0, 2):
+        lat, sigma, walls, tau, g, nstar, seed = PORES[k]
+        n, u = pore_fields(lat, sigma, walls, nstar, seed)
+        s = w.wdlb_batch_add(b, lat, sigma, walls, tau, g, n, u)
+        o = oracle_mod.Oracle(*lat, walls, sigma, tau, g)
+        o.init(n, u)
+        ref.append((s, o, walls))
+    w.wdlb_batch_step(b, 30)
+    for s, o, walls in ref:
+        o.step(30)
+        n_g, u_g = w.wdlb_moments(w.wdlb_batch_context(b, s))
+        n_o, u_o = o.moments()
+        m = slice(1, -1) if walls else slice(None)
+        np.testing.assert_allclose(n_g[m], n_o[m], rtol=1e-10)
+        np.testing.assert_allclose(u_g[:, m], u_o[:, m], rtol=0, atol=1e-10 * np.abs(u_o[:, m]).max())
+    w.wdlb_batch_destroy(b)
+
+
+def test_batch_residuals_and_status(w):
+    b = w.wdlb_batch_create(4, 32 << 20, storage="f32", interactions=False)
+    n = np.full((21, 4, 4), 0.01)
+    s = w.wdlb_batch_add(b, (4, 4, 21), 4.0, True, 0.5 + 3 ** 0.5 / 4, (1e-6, 0, 0), n)
+    w.wdlb_batch_residuals(b, 100)
+    res = None
+    for _ in range(60):
+        w.wdlb_batch_step(b, 100)
+        res, st = w.wdlb_batch_residuals(b, 100)
+        if res[s] < 1e-7:
+            break
+    assert res[s] < 1e-7 and st[s] == 0
+    assert np.isnan(res[(s + 1) % 4]) and st[(s + 1) % 4] == -1
+    w.wdlb_batch_destroy(b)
