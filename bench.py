@@ -174,6 +174,46 @@ def cpu_baseline_oracle(timesteps=1, box=L):
                       % (timesteps, box, dt)}
 
 
+def run_serving(w, synth, np, rate, window_s, drain_s):
+    """Continuous-batching server fed with Poisson arrivals in real time; each
+    request runs to a 1e-8 steady state.  Requests arrive for window_s seconds,
+    then the server drains for up to drain_s seconds; latency = finish - submit."""
+    reqs = synth.serving_requests(rate, window_s)
+    srv = w.wdlb_server_create(24 << 30, max_active=1024, check_every=100)
+    submitted = {}
+    t_start = time.perf_counter()
+    for t_arr, q, seed in reqs:
+        now = time.perf_counter() - t_start
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        pp, n, u = synth.slit_poiseuille(q["nx"], q["ny"], q["nz"], q["n_star"], q["sigma"], q["tau"], q["gx"], seed)
+        rid = w.wdlb_server_submit(srv, (q["nx"], q["ny"], q["nz"]), q["sigma"], True, q["tau"], pp["g"], n, u,
+                                   tol=1e-8, max_steps=10 ** 7)
+        submitted[rid] = q
+    done = []
+    while time.perf_counter() - t_start < window_s + drain_s:
+        done.extend(w.wdlb_server_poll(srv))
+        if len(done) == len(submitted):
+            break
+        time.sleep(0.02)
+    elapsed = time.perf_counter() - t_start
+    done.extend(w.wdlb_server_poll(srv))
+    info = w.wdlb_server_info(srv)
+    w.wdlb_server_destroy(srv)
+    ok = [r for r in done if r["status"] == 0]
+    lat = np.array([r["finish_s"] - r["submit_s"] for r in ok]) if ok else np.array([np.nan])
+    node_steps = sum(submitted[r["id"]]["nx"] * submitted[r["id"]]["ny"] * submitted[r["id"]]["nz"] * r["steps"]
+                     for r in ok)
+    return {"offered_rate_per_s": rate, "arrival_window_s": window_s, "submitted": len(submitted),
+            "completed": len(ok), "failed": len(done) - len(ok), "elapsed_s": elapsed,
+            "solves_per_s": len(ok) / elapsed, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "backlog_at_end": info["queued"] + info["active"],
+            "completed_mlups": node_steps / elapsed / 1e6, "tolerance": 1e-8,
+            "workload": "slit Poiseuille requests: sigma in {3,4,6}, H/sigma lognormal (median 10, log-sd 0.5) "
+                        "clipped to [3,60], x-y 16..64, n* in [0.1,0.6], g_x log-uniform [1e-7,1e-5], tau=1, "
+                        "FP32, 24 GiB admission budget"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -338,6 +378,11 @@ def run_ours(args):
                            "[1e-7, 1e-5], tau=1, FP32; one launch per phase for all pores, CUDA graph"}
     w.wdlb_batch_destroy(bt)
 
+    # ---------------- serving: Poisson arrivals of steady-state slit solves ----------------
+    serve = None
+    if not args.no_serve:
+        serve = run_serving(w, synth, np, rate=200.0, window_s=5.0, drain_s=25.0)
+
     # ---------------- other storage paths (same workload, shorter) ----------------
     paths = {}
     for storage, sub, reps in (("f64", 10, 2), ("f16", SUB, 3)):
@@ -401,7 +446,7 @@ def run_ours(args):
                     "path": "wdlb_init_fields(host) + wdlb_step(100) + wdlb_moments(host), pinned buffers"},
             "clocks": clocks, "gpu_launches": int(gpu_launches),
             "kernels_ms": {"moments": kms[0], "smeared_density": kms[1], "shell_collide_stream": kms[2]},
-            "paths": paths, "batched": batched, "pore_average": {k: stats[k] for k in ("mass", "mean_n", "mean_ux", "steps")}}
+            "paths": paths, "batched": batched, "serve": serve, "pore_average": {k: stats[k] for k in ("mass", "mean_n", "mean_ux", "steps")}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -416,6 +461,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--only-device", action="store_true",
                     help="time only the device-resident loop (for profiling); no e2e, baseline or other paths")
     ap.add_argument("--sub", type=int, default=SUB, help="lattice time steps per benchmark step")

@@ -234,6 +234,53 @@ int64_t wdlb_batch_launch_count(const wdlb_batch *b);
 const char *wdlb_batch_last_error(const wdlb_batch *b);
 void wdlb_batch_destroy(wdlb_batch *b);
 
+/* ---- Serving: continuous batching of steady-state solves ----------------
+ * Requests (a pore, its initial fields and a steady-state tolerance) arrive
+ * at any time from any thread.  A worker thread of the server admits queued
+ * requests into a batch while the HBM budget (the batch pool) has room, steps
+ * all admitted pores together in blocks of check_every steps, tests each
+ * pore's FP64 residual (as wdlb_run_steady) after every block, and retires
+ * converged pores (status WDLB_OK), pores that reach max_steps
+ * (WDLB_ERR_TIMEOUT) or become non-physical (WDLB_ERR_UNSTABLE); a pore larger
+ * than the whole budget is rejected (WDLB_ERR_OOM).  Each request's result is
+ * the same as solving it alone with wdlb_run_steady(tol, check_every). */
+typedef struct wdlb_server wdlb_server;
+typedef struct {
+    wdlb_pore_desc desc;
+    const double *n, *u;      /* initial fields (host; copied by submit; u may be NULL) */
+    double tol;               /* steady-state tolerance (> 0)                        */
+    int64_t max_steps;        /* give up after this many steps (>= 1)                */
+    double *out_n, *out_u;    /* optional host buffers (N, 3N doubles) for the final
+                                 moments; valid until the result is polled           */
+} wdlb_request;
+typedef struct {
+    int64_t id;
+    int32_t status;
+    int64_t steps;
+    double residual;
+    double submit_s, start_s, finish_s;   /* server clock (seconds since creation) */
+    wdlb_pore_stats stats;
+} wdlb_result;
+typedef struct {
+    int64_t submitted, admitted, completed, queued, active;
+    uint64_t pool_free;
+    int64_t launches;
+    double clock_s;
+} wdlb_server_stats;
+
+/* opt as for wdlb_batch_create; hbm_budget: pool bytes for admitted pores;
+ * max_active: slots; check_every: steps between residual tests.  Starts the
+ * worker thread on the current device. */
+wdlb_status wdlb_server_create(const wdlb_options *opt, uint64_t hbm_budget, int32_t max_active,
+                               int32_t check_every, wdlb_server **out);
+/* Queue a request (thread-safe, returns at once); *id identifies its result. */
+wdlb_status wdlb_server_submit(wdlb_server *s, const wdlb_request *r, int64_t *id);
+/* Move up to cap finished results into out; returns how many. */
+int32_t wdlb_server_poll(wdlb_server *s, wdlb_result *out, int32_t cap);
+wdlb_status wdlb_server_info(wdlb_server *s, wdlb_server_stats *info);
+/* Stop the worker (unfinished requests are dropped) and free everything. */
+void wdlb_server_destroy(wdlb_server *s);
+
 /* ---- Fields without any device allocation --------------------------------
  * No counterpart in the paper: an entry point for callers that cannot
  * allocate device memory (code that runs inside another framework's memory

@@ -1086,3 +1086,255 @@ void wdlb_batch_destroy(wdlb_batch *b)
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Serving loop: requests arrive at any time (wdlb_server_submit, any thread);
+// a worker thread admits them into a batch while its pool has room, steps all
+// admitted pores together in blocks of check_every steps, tests every pore's
+// FP64 steady-state residual after each block and retires the converged ones
+// (continuous batching: admissions and retirements interleave with steps).
+// ===========================================================================
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+
+struct wdlb_server {
+    wdlb_batch *batch = nullptr;
+    int device = 0;
+    int32_t check_every = 100;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    struct Pending {
+        int64_t id;
+        wdlb_request req;
+        std::vector<double> n, u;
+        double submit_s;
+    };
+    struct Active {
+        int64_t id;
+        wdlb_request req;
+        double submit_s, start_s;
+    };
+    std::deque<Pending> queue;
+    std::vector<Active> active;   // indexed by slot
+    std::vector<wdlb_result> done;
+    int64_t next_id = 1, submitted = 0, admitted = 0, completed = 0;
+    std::chrono::steady_clock::time_point t0;
+    std::string err;
+};
+
+namespace {
+
+double server_now(const wdlb_server *s)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+}
+
+void server_finish(wdlb_server *s, int slot, int32_t status, double residual)
+{
+    wdlb_server::Active a = s->active[slot];
+    wdlb_ctx *c = wdlb_batch_context(s->batch, slot);
+    wdlb_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.id = a.id;
+    r.status = status;
+    r.residual = residual;
+    r.submit_s = a.submit_s;
+    r.start_s = a.start_s;
+    if (c) {
+        r.steps = c->steps;
+        if (wdlb_pore_average(c, &r.stats) != WDLB_OK && r.status == WDLB_OK) r.status = WDLB_ERR_UNSTABLE;
+        r.stats.residual = residual;
+        if (a.req.out_n || a.req.out_u) wdlb_moments(c, a.req.out_n, a.req.out_u);
+    }
+    wdlb_batch_remove(s->batch, slot);
+    r.finish_s = server_now(s);
+    s->active[slot].id = 0;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->done.push_back(r);
+    s->completed++;
+}
+
+void server_loop(wdlb_server *s)
+{
+    cudaSetDevice(s->device);
+    std::vector<double> res(s->active.size()), tmp;
+    std::vector<int32_t> st(s->active.size());
+    for (;;) {
+        // admit while there is room
+        bool admitted_now = false;
+        for (;;) {
+            wdlb_server::Pending p;
+            {
+                std::unique_lock<std::mutex> lock(s->mu);
+                if (s->stop) return;
+                if (s->queue.empty()) {
+                    if (wdlb_batch_active(s->batch) == 0) {
+                        s->cv.wait_for(lock, std::chrono::milliseconds(2));
+                        continue;
+                    }
+                    break;
+                }
+                uint64_t need = 0;
+                if (wdlb_batch_pore_bytes(s->batch, &s->queue.front().req.desc, &need) != WDLB_OK) need = 0;
+                if (need == 0 || need > wdlb_batch_free_bytes(s->batch)) {
+                    if (wdlb_batch_active(s->batch) == 0 && need != 0) {
+                        // larger than the whole pool: reject it
+                        p = std::move(s->queue.front());
+                        s->queue.pop_front();
+                        lock.unlock();
+                        wdlb_result r;
+                        std::memset(&r, 0, sizeof(r));
+                        r.id = p.id;
+                        r.status = WDLB_ERR_OOM;
+                        r.submit_s = r.start_s = p.submit_s;
+                        r.finish_s = server_now(s);
+                        std::lock_guard<std::mutex> l2(s->mu);
+                        s->done.push_back(r);
+                        s->completed++;
+                        continue;
+                    }
+                    break;
+                }
+                p = std::move(s->queue.front());
+                s->queue.pop_front();
+            }
+            int32_t slot = -1;
+            wdlb_status a = wdlb_batch_add(s->batch, &p.req.desc, p.n.data(), p.u.empty() ? nullptr : p.u.data(), &slot);
+            if (a != WDLB_OK) {
+                std::lock_guard<std::mutex> lock(s->mu);
+                if (a == WDLB_ERR_OOM) {   // fragmentation or slots: retry later
+                    s->queue.push_front(std::move(p));
+                    break;
+                }
+                wdlb_result r;
+                std::memset(&r, 0, sizeof(r));
+                r.id = p.id;
+                r.status = a;
+                r.submit_s = r.start_s = p.submit_s;
+                r.finish_s = server_now(s);
+                s->done.push_back(r);
+                s->completed++;
+                continue;
+            }
+            s->active[slot] = wdlb_server::Active{p.id, p.req, p.submit_s, server_now(s)};
+            s->active[slot].req.n = s->active[slot].req.u = nullptr;
+            s->admitted++;
+            admitted_now = true;
+        }
+        // u_x snapshot of the new pores (the others' snapshots are re-taken at the same state)
+        if (admitted_now) wdlb_batch_residuals(s->batch, s->check_every, res.data(), st.data());
+        if (wdlb_batch_active(s->batch) == 0) continue;
+        // one block of steps for every admitted pore, then the residual test
+        if (wdlb_batch_step(s->batch, s->check_every) != WDLB_OK ||
+            wdlb_batch_residuals(s->batch, s->check_every, res.data(), st.data()) != WDLB_OK) {
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->err = wdlb_batch_last_error(s->batch);
+            for (size_t k = 0; k < s->active.size(); k++)
+                if (s->active[k].id) st[k] = WDLB_ERR_CUDA;
+        }
+        for (size_t k = 0; k < s->active.size(); k++) {
+            if (!s->active[k].id) continue;
+            wdlb_ctx *c = wdlb_batch_context(s->batch, (int)k);
+            const wdlb_request &q = s->active[k].req;
+            if (st[k] != WDLB_OK)
+                server_finish(s, (int)k, st[k], res[k]);
+            else if (res[k] < q.tol)
+                server_finish(s, (int)k, WDLB_OK, res[k]);
+            else if (c && c->steps >= q.max_steps)
+                server_finish(s, (int)k, WDLB_ERR_TIMEOUT, res[k]);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+wdlb_status wdlb_server_create(const wdlb_options *opt, uint64_t hbm_budget, int32_t max_active, int32_t check_every,
+                               wdlb_server **out)
+{
+    if (!out || check_every < 1) return WDLB_ERR_ARG;
+    *out = nullptr;
+    wdlb_server *s = new (std::nothrow) wdlb_server();
+    if (!s) return WDLB_ERR_OOM;
+    cudaGetDevice(&s->device);
+    wdlb_status st = wdlb_batch_create(opt, hbm_budget, max_active, &s->batch);
+    if (st != WDLB_OK) {
+        delete s;
+        return st;
+    }
+    s->check_every = check_every;
+    s->active.resize(max_active);
+    for (auto &a : s->active) a.id = 0;
+    s->t0 = std::chrono::steady_clock::now();
+    s->worker = std::thread(server_loop, s);
+    *out = s;
+    return WDLB_OK;
+}
+
+wdlb_status wdlb_server_submit(wdlb_server *s, const wdlb_request *r, int64_t *id)
+{
+    if (!s || !r || !r->n || !(r->tol > 0) || r->max_steps < 1) return WDLB_ERR_ARG;
+    wdlb_lattice lat = r->desc.lat;
+    if (lat.nx < 1 || lat.ny < 1 || lat.nz < 1) return WDLB_ERR_ARG;
+    const size_t N = (size_t)lat.nx * lat.ny * lat.nz;
+    wdlb_server::Pending p;
+    p.req = *r;
+    p.n.assign(r->n, r->n + N);
+    if (r->u) p.u.assign(r->u, r->u + 3 * N);
+    p.submit_s = server_now(s);
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        p.id = s->next_id++;
+        s->submitted++;
+        if (id) *id = p.id;
+        s->queue.push_back(std::move(p));
+    }
+    s->cv.notify_one();
+    return WDLB_OK;
+}
+
+int32_t wdlb_server_poll(wdlb_server *s, wdlb_result *out, int32_t cap)
+{
+    if (!s || !out || cap < 1) return 0;
+    std::lock_guard<std::mutex> lock(s->mu);
+    int32_t n = (int32_t)std::min<size_t>(cap, s->done.size());
+    for (int32_t k = 0; k < n; k++) out[k] = s->done[k];
+    s->done.erase(s->done.begin(), s->done.begin() + n);
+    return n;
+}
+
+wdlb_status wdlb_server_info(wdlb_server *s, wdlb_server_stats *info)
+{
+    if (!s || !info) return WDLB_ERR_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    info->submitted = s->submitted;
+    info->admitted = s->admitted;
+    info->completed = s->completed;
+    info->queued = (int64_t)s->queue.size();
+    info->active = wdlb_batch_active(s->batch);
+    info->pool_free = wdlb_batch_free_bytes(s->batch);
+    info->launches = wdlb_batch_launch_count(s->batch);
+    info->clock_s = server_now(s);
+    return WDLB_OK;
+}
+
+void wdlb_server_destroy(wdlb_server *s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    wdlb_batch_destroy(s->batch);
+    delete s;
+}
+
+}  // extern "C"

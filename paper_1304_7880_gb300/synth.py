@@ -106,3 +106,31 @@ def batched_pores(count: int = 64, seed: int = 4, sigma: float = 4.0, nxy: int =
         gx = 10.0 ** (-7.0 + 2.0 * U[p, 2])
         out.append(slit_poiseuille(nxy, nxy, nz, n_star, sigma, 1.0, gx, seed * 1000 + p))
     return out
+
+
+def serving_requests(rate: float, window_s: float, seed: int = 5, n_star_max: float = 0.6, ln_sigma: float = 0.5):
+    """Poisson arrivals (mean rate per second) over window_s seconds of slit
+    Poiseuille requests: sigma in {3, 4, 6}; H/sigma lognormal with median 10
+    and log-standard deviation ln_sigma, clipped to [3, 60]; nx = ny uniform in
+    16..64; n* uniform in [0.1, n_star_max]; g_x log-uniform in [1e-7, 1e-5];
+    tau = 1.  Returns (arrival_time, params, seed) tuples; slit_poiseuille with
+    those parameters and seed makes the fields."""
+    out = []
+    t = 0.0
+    k = 0
+    while True:
+        U = uniform01(seed, 8, offset=8 * k)
+        t += -math.log(1.0 - U[0]) / rate
+        if t > window_s:
+            break
+        sigma = (3.0, 4.0, 6.0)[min(2, int(U[1] * 3))]
+        # Box-Muller normal from two uniforms
+        z = math.sqrt(-2.0 * math.log(1.0 - U[2])) * math.cos(2.0 * math.pi * U[3])
+        h = min(60.0, max(3.0, 10.0 * math.exp(ln_sigma * z)))
+        nz = int(round(h * sigma)) + 1
+        nxy = 16 + min(48, int(U[4] * 49))
+        n_star = 0.1 + (n_star_max - 0.1) * U[5]
+        gx = 10.0 ** (-7.0 + 2.0 * U[6])
+        out.append((t, dict(nx=nxy, ny=nxy, nz=nz, n_star=n_star, sigma=sigma, tau=1.0, gx=gx), seed * 100000 + k))
+        k += 1
+    return out

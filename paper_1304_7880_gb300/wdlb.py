@@ -49,6 +49,17 @@ class wdlb_pore_desc(ctypes.Structure):
                 ("tau", ctypes.c_double), ("g", ctypes.c_double * 3)]
 
 
+class wdlb_request(ctypes.Structure):
+    _fields_ = [("desc", wdlb_pore_desc), ("n", ctypes.c_void_p), ("u", ctypes.c_void_p), ("tol", ctypes.c_double),
+                ("max_steps", ctypes.c_int64), ("out_n", ctypes.c_void_p), ("out_u", ctypes.c_void_p)]
+
+
+class wdlb_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("active", ctypes.c_int64), ("pool_free", ctypes.c_uint64),
+                ("launches", ctypes.c_int64), ("clock_s", ctypes.c_double)]
+
+
 class wdlb_pore_stats(ctypes.Structure):
     _fields_ = [("mean_n", ctypes.c_double), ("mean_ux", ctypes.c_double), ("flux_x", ctypes.c_double),
                 ("mass", ctypes.c_double), ("eta_eff", ctypes.c_double), ("residual", ctypes.c_double),
@@ -95,6 +106,11 @@ def load_library(path: str = LIB_PATH):
         "wdlb_batch_launch_count": (I64, [P]),
         "wdlb_batch_last_error": (ctypes.c_char_p, [P]),
         "wdlb_batch_destroy": (None, [P]),
+        "wdlb_server_create": (I32, [P, ctypes.c_uint64, I32, I32, P]),
+        "wdlb_server_submit": (I32, [P, P, P]),
+        "wdlb_server_poll": (I32, [P, P, I32]),
+        "wdlb_server_info": (I32, [P, P]),
+        "wdlb_server_destroy": (None, [P]),
         "wdlb_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -419,3 +435,104 @@ def wdlb_batch_destroy(batch):
     if batch.handle:
         load_library().wdlb_batch_destroy(batch.handle)
         batch.handle = None
+
+
+# ---- serving ---------------------------------------------------------------------------
+
+class wdlb_result(ctypes.Structure):
+    pass
+
+
+class Server:
+    def __init__(self, handle, pool, stream):
+        self.handle = handle
+        self.pool = pool
+        self.stream = stream
+        self.keep = {}     # id -> host arrays that must outlive the request
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            wdlb_server_destroy(self)
+
+
+def wdlb_server_create(hbm_budget, max_active=256, check_every=100, closure="CS", storage="f32", device=None):
+    """Serving loop (native worker thread) over a batch whose pool is a torch tensor."""
+    import torch
+
+    lib = load_library()
+    opt = wdlb_options()
+    lib.wdlb_default_options(ctypes.byref(opt))
+    opt.closure = CLOSURES[closure]
+    opt.storage = STORAGES[storage]
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    pool = torch.empty(int(hbm_budget) + 256, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize(dev)
+    opt.workspace = ctypes.c_void_p((pool.data_ptr() + 255) & ~255)
+    opt.workspace_bytes = int(hbm_budget)
+    opt.stream = ctypes.c_void_p(stream.cuda_stream)
+    h = ctypes.c_void_p()
+    with torch.cuda.device(dev):
+        st = lib.wdlb_server_create(ctypes.byref(opt), int(hbm_budget), int(max_active), int(check_every),
+                                    ctypes.byref(h))
+    if st != WDLB_OK:
+        raise WDLBError(st, "wdlb_server_create")
+    return Server(h, pool, stream)
+
+
+def wdlb_server_submit(server, lattice, sigma, walls, tau, g, n, u=None, tol=1e-8, max_steps=10 ** 7,
+                       want_moments=False) -> int:
+    nx, ny, nz = (int(v) for v in lattice)
+    shape = (nz, ny, nx)
+    nn = _f64(n, shape)
+    uu = None if u is None else _f64(u, (3,) + shape)
+    r = wdlb_request()
+    r.desc = _desc(lattice, sigma, walls, tau, g)
+    r.n = nn.ctypes.data
+    r.u = None if uu is None else uu.ctypes.data
+    r.tol = float(tol)
+    r.max_steps = int(max_steps)
+    outs = None
+    if want_moments:
+        outs = (np.zeros(shape), np.zeros((3,) + shape))
+        r.out_n = outs[0].ctypes.data
+        r.out_u = outs[1].ctypes.data
+    rid = ctypes.c_int64()
+    st = load_library().wdlb_server_submit(server.handle, ctypes.byref(r), ctypes.byref(rid))
+    if st != WDLB_OK:
+        raise WDLBError(st, "wdlb_server_submit")
+    server.keep[rid.value] = outs
+    return rid.value
+
+
+def wdlb_server_poll(server, cap=1024):
+    """Finished results: list of dicts (with 'n', 'u' if moments were requested)."""
+    buf = (wdlb_result * cap)()
+    k = load_library().wdlb_server_poll(server.handle, buf, cap)
+    out = []
+    for r in buf[:k]:
+        d = {"id": r.id, "status": r.status, "steps": r.steps, "residual": r.residual, "submit_s": r.submit_s,
+             "start_s": r.start_s, "finish_s": r.finish_s,
+             "stats": {f: getattr(r.stats, f) for f, _ in wdlb_pore_stats._fields_}}
+        outs = server.keep.pop(r.id, None)
+        if outs is not None:
+            d["n"], d["u"] = outs
+        out.append(d)
+    return out
+
+
+def wdlb_server_info(server) -> dict:
+    st = wdlb_server_stats()
+    load_library().wdlb_server_info(server.handle, ctypes.byref(st))
+    return {f: getattr(st, f) for f, _ in wdlb_server_stats._fields_}
+
+
+def wdlb_server_destroy(server):
+    if server.handle:
+        load_library().wdlb_server_destroy(server.handle)
+        server.handle = None
+
+
+wdlb_result._fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("steps", ctypes.c_int64),
+                        ("residual", ctypes.c_double), ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                        ("finish_s", ctypes.c_double), ("stats", wdlb_pore_stats)]
