@@ -158,9 +158,12 @@ typedef struct {
 wdlb_status wdlb_pore_average(wdlb_ctx *ctx, wdlb_pore_stats *out);
 
 /* Steady-state driver: step in blocks of check_every (>= 1) steps; after each
- * block compute in FP64 r = max|u_x(t) - u_x(t - check_every)| /
- * (check_every * max|u_x(t)|) and stop when r < tol or after max_steps.
- * *steps_done and *residual (either may be NULL) report the outcome. */
+ * block compute in FP64 the relative change per step of the pore flux
+ * Q = sum(n u_x) over fluid nodes, r = |Q(t) - Q(t - check_every)| /
+ * (check_every |Q(t)|), and stop when r < tol or after max_steps.  (A max-norm
+ * change of u_x stalls near 2e-7 in FP32: rounding jitter next to the walls;
+ * the flux averages it out.)  *steps_done and *residual (either may be NULL)
+ * report the outcome. */
 wdlb_status wdlb_run_steady(wdlb_ctx *ctx, double tol, int32_t check_every, int64_t max_steps,
                             int64_t *steps_done, double *residual);
 
@@ -219,10 +222,11 @@ wdlb_status wdlb_batch_add(wdlb_batch *b, const wdlb_pore_desc *d, const double 
 wdlb_status wdlb_batch_remove(wdlb_batch *b, int32_t slot);
 /* Steps 2-5 of the algorithm of Sec. 5 for every pore, nsteps times (async). */
 wdlb_status wdlb_batch_step(wdlb_batch *b, int64_t nsteps);
-/* Per slot (array of max_pores): the FP64 steady-state residual
- * max|u_x - u_x(previous call)| / (interval max|u_x|) (NaN for empty slots)
- * and the slot status (WDLB_OK, WDLB_ERR_UNSTABLE, -1 empty); either array
- * may be NULL.  Updates each pore's u_x snapshot.  Synchronous. */
+/* Per slot (array of max_pores): the FP64 steady-state residual of
+ * wdlb_run_steady, |Q - Q(previous call)| / (interval |Q|) with Q the pore flux
+ * (+inf at a pore's first call, NaN for empty slots), and the slot status
+ * (WDLB_OK, WDLB_ERR_UNSTABLE, -1 empty); either array may be NULL.
+ * Synchronous. */
 wdlb_status wdlb_batch_residuals(wdlb_batch *b, int32_t interval, double *res, int32_t *status);
 /* The context of a slot (owned by the batch): use it for wdlb_moments,
  * wdlb_pore_average, wdlb_fields, wdlb_get_populations; do not step or
@@ -266,6 +270,7 @@ typedef struct {
     uint64_t pool_free;
     int64_t launches;
     double clock_s;
+    int64_t node_steps;       /* lattice-node updates executed so far */
 } wdlb_server_stats;
 
 /* opt as for wdlb_batch_create; hbm_budget: pool bytes for admitted pores;

@@ -101,6 +101,7 @@ struct wdlb_ctx {
     int64_t steps = 0;
     int64_t launches = 0;
     double last_residual = NAN;
+    double prev_flux = NAN;        // pore flux at the last residual test
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> prof_events;   // event pool of wdlb_profile_step
     const Launchers *L = nullptr;
@@ -233,6 +234,7 @@ wdlb_status init_from_stage(wdlb_ctx *ctx, const double *d_n, const double *d_u)
     ctx->initialised = true;
     ctx->steps = 0;
     ctx->last_residual = NAN;
+    ctx->prev_flux = NAN;
     return WDLB_OK;
 }
 
@@ -547,6 +549,22 @@ wdlb_status wdlb_pore_average(wdlb_ctx *ctx, wdlb_pore_stats *out)
     return WDLB_OK;
 }
 
+// Steady-state residual: relative change per step of the pore flux sum(n u_x)
+// (FP64 reduction) between two tests `interval` steps apart.
+double flux_residual(wdlb_ctx *ctx, const double r[6], int64_t interval)
+{
+    const double q = r[2];
+    double res;
+    if (!std::isfinite(ctx->prev_flux))
+        res = INFINITY;
+    else if (q == 0.0)
+        res = q == ctx->prev_flux ? 0.0 : INFINITY;
+    else
+        res = std::fabs(q - ctx->prev_flux) / (double(interval) * std::fabs(q));
+    ctx->prev_flux = q;
+    return res;
+}
+
 wdlb_status wdlb_run_steady(wdlb_ctx *ctx, double tol, int32_t check_every, int64_t max_steps,
                             int64_t *steps_done, double *residual)
 {
@@ -556,6 +574,7 @@ wdlb_status wdlb_run_steady(wdlb_ctx *ctx, double tol, int32_t check_every, int6
     double r[6];
     wdlb_status s = stats(ctx, 1, r);
     if (s != WDLB_OK) return s;
+    ctx->prev_flux = r[2];
     int64_t done = 0;
     double res = NAN;
     while (done < max_steps) {
@@ -565,7 +584,7 @@ wdlb_status wdlb_run_steady(wdlb_ctx *ctx, double tol, int32_t check_every, int6
         done += n;
         s = stats(ctx, 1, r);
         if (s != WDLB_OK) return s;
-        res = r[4] > 0 ? r[3] / (double(n) * r[4]) : 0.0;
+        res = flux_residual(ctx, r, n);
         ctx->last_residual = res;
         if (res < tol) break;
     }
@@ -1034,7 +1053,7 @@ wdlb_status wdlb_batch_residuals(wdlb_batch *b, int32_t interval, double *res, i
         wdlb_ctx *c = b->slots[s].ctx;
         double v = NAN;
         if (c) {
-            v = r[6 * s + 4] > 0 ? r[6 * s + 3] / (double(interval) * r[6 * s + 4]) : 0.0;
+            v = flux_residual(c, &r[6 * s], interval);
             c->last_residual = v;
         }
         if (res) res[s] = v;
@@ -1123,6 +1142,7 @@ struct wdlb_server {
     std::vector<Active> active;   // indexed by slot
     std::vector<wdlb_result> done;
     int64_t next_id = 1, submitted = 0, admitted = 0, completed = 0;
+    int64_t node_steps = 0;       // lattice-node updates executed
     std::chrono::steady_clock::time_point t0;
     std::string err;
 };
@@ -1229,7 +1249,17 @@ void server_loop(wdlb_server *s)
         // u_x snapshot of the new pores (the others' snapshots are re-taken at the same state)
         if (admitted_now) wdlb_batch_residuals(s->batch, s->check_every, res.data(), st.data());
         if (wdlb_batch_active(s->batch) == 0) continue;
+        int64_t block_nodes = 0;
+        for (size_t k = 0; k < s->active.size(); k++)
+            if (s->active[k].id) {
+                wdlb_ctx *c = wdlb_batch_context(s->batch, (int)k);
+                if (c) block_nodes += c->N;
+            }
         // one block of steps for every admitted pore, then the residual test
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->node_steps += block_nodes * s->check_every;
+        }
         if (wdlb_batch_step(s->batch, s->check_every) != WDLB_OK ||
             wdlb_batch_residuals(s->batch, s->check_every, res.data(), st.data()) != WDLB_OK) {
             std::lock_guard<std::mutex> lock(s->mu);
@@ -1321,6 +1351,7 @@ wdlb_status wdlb_server_info(wdlb_server *s, wdlb_server_stats *info)
     info->pool_free = wdlb_batch_free_bytes(s->batch);
     info->launches = wdlb_batch_launch_count(s->batch);
     info->clock_s = server_now(s);
+    info->node_steps = s->node_steps;
     return WDLB_OK;
 }
 
