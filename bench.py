@@ -136,7 +136,7 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_shell_tiled_bulk128_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_shell_tiled_bulk128_traffic.txt")
 
 
 def recorded_traffic():
@@ -447,7 +447,7 @@ def run_ours(args):
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     step_ms = sum(kms)
     hbm_achieved = BYTES_PER_NODE["f32"] * N / (step_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "k_shell_tiled", "achieved": achieved_tflops, "peak": alu_peak,
+    roofline = {"bound": "alu", "kernel": "k_step_shell_tiled", "achieved": achieved_tflops, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak, "traffic": recorded_traffic(),
                 "peak_source": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts)",
                 "flops_per_node": flops_per_node,

@@ -38,13 +38,25 @@ struct Tables {
 };
 
 struct Layout {
-    size_t f[2], nu, hb, cprev, tprev, nscale, stage, snap, partial, result, status, shell_e, shell_k, ball, total;
+    size_t f[2], nu, hb, cprev, tprev, nscale, stage, snap, partial, result, status, shell_e, shell_k, ball;
+    size_t params, kbufs, items;   // one-slot step tables (KParams, KBufs of both parities, work items)
+    size_t nitems;
+    size_t total;
 };
 
 int storage_bytes(int storage) { return storage == WDLB_STORE_F64 ? 8 : (storage == WDLB_STORE_F32 ? 4 : 2); }
 int compute_bytes(int storage) { return storage == WDLB_STORE_F64 ? 8 : 4; }
 
-Layout layout_for(long long N, long long Npad, int storage, int nshell, int nball)
+// Work items of a lattice stepped alone: blocks of 256 nodes for the moments,
+// and bricks or blocks for the smeared density and the shell sums.
+size_t step_items(wdlb_lattice lat, long long N)
+{
+    const size_t nb = size_t((N + 255) / 256);
+    const size_t nt = size_t((lat.nx + 7) / 8) * size_t((lat.ny + 7) / 8) * size_t((lat.nz + 7) / 8);
+    return nb + 2 * std::max(nb, nt);
+}
+
+Layout layout_for(wdlb_lattice lat, long long N, long long Npad, int storage, int nshell, int nball)
 {
     Layout L;
     size_t off = 0;
@@ -69,6 +81,10 @@ Layout layout_for(long long N, long long Npad, int storage, int nshell, int nbal
     L.shell_e = take(std::max(nshell, 1) * sizeof(int4));
     L.shell_k = take(std::max(nshell, 1) * 4 * sT);
     L.ball = take(std::max(nball, 1) * sizeof(int4));
+    L.params = take(sizeof(KParams));
+    L.kbufs = take(2 * kKBufsMaxBytes);
+    L.nitems = step_items(lat, N);
+    L.items = take(L.nitems * sizeof(BatchItem));
     L.total = off;
     return L;
 }
@@ -103,6 +119,7 @@ struct wdlb_ctx {
     double last_residual = NAN;
     double prev_flux = NAN;        // pore flux at the last residual test
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    BatchLaunch launch{};          // one-slot step tables in device memory (bufs[p]: input buffer p)
     std::vector<cudaEvent_t> prof_events;   // event pool of wdlb_profile_step
     const Launchers *L = nullptr;
     std::string err;
@@ -190,6 +207,10 @@ void set_params(wdlb_ctx *ctx)
     const double s2 = 2.0 * ctx->sigma;
     p.s2 = (std::fabs(s2 - std::round(s2)) < 1e-12) ? (int)std::lround(s2) : 0;
     p.tiled = 0;
+    p.ball_r = 0;
+    for (size_t m = 0; m < ctx->tab.ball.size(); m++) p.ball_r = std::max(p.ball_r, std::abs(ctx->tab.ball[m]));
+    const size_t tsize = ctx->opt.storage == WDLB_STORE_F64 ? sizeof(double) : sizeof(float);
+    p.ball_tiled = ball_tile_smem(p.ball_r, p.nball, tsize) <= kBallTileMaxSmem ? 1 : 0;
     // n_off / ref_ng are set at init (they may depend on the initial state)
 }
 
@@ -210,6 +231,70 @@ void drop_graphs(wdlb_ctx *ctx)
         }
 }
 
+// One-slot step tables of a lattice stepped alone: its parameters, its
+// buffers for both input parities and its work items, so that it runs the
+// same kernels as a slot of a batch.  Synchronous (host vectors).
+cudaError_t upload_step_tables(wdlb_ctx *ctx)
+{
+    char *b = ctx->base;
+    const Layout &L = ctx->lay;
+    const KParams &p = ctx->kp;
+    std::vector<char> kb(2 * kKBufsMaxBytes, 0);
+    ctx->L->kbufs_fill(ctx->dev, 0, kb.data());
+    ctx->L->kbufs_fill(ctx->dev, 1, kb.data() + kKBufsMaxBytes);
+    std::vector<BatchItem> items;
+    const int nb = (int)((ctx->N + 255) / 256);
+    const int tx = (p.nx + 7) / 8, ty = (p.ny + 7) / 8, tz = (p.nz + 7) / 8;
+    auto bricks = [&]() {
+        for (int z = 0; z < tz; z++)
+            for (int y = 0; y < ty; y++)
+                for (int x = 0; x < tx; x++) items.push_back(BatchItem{0, x, y, z});
+    };
+    auto blocks = [&]() {
+        for (int k = 0; k < nb; k++) items.push_back(BatchItem{0, k, 0, 0});
+    };
+    BatchLaunch &LL = ctx->launch;
+    LL = BatchLaunch{};
+    LL.params = reinterpret_cast<const KParams *>(b + L.params);
+    LL.bufs[0] = b + L.kbufs;
+    LL.bufs[1] = b + L.kbufs + kKBufsMaxBytes;
+    const BatchItem *dit = reinterpret_cast<const BatchItem *>(b + L.items);
+    LL.node_items = dit;
+    blocks();
+    LL.n_node_items = nb;
+    if (p.ball_tiled) {
+        LL.ball_items = dit + items.size();
+        bricks();
+        LL.n_ball_items = tx * ty * tz;
+        LL.ball_smem = ball_tile_smem(p.ball_r, p.nball, ctx->opt.storage == WDLB_STORE_F64 ? 8 : 4);
+    } else {
+        LL.ball_node_items = dit + items.size();
+        blocks();
+        LL.n_ball_node_items = nb;
+    }
+    BatchGroup &G = LL.groups[0];
+    G.s2 = p.tiled ? p.s2 : 0;
+    G.walls = ctx->walls;
+    G.tiled = p.tiled;
+    G.closure = p.closure;
+    G.items = dit + items.size();
+    if (p.tiled)
+        bricks();
+    else
+        blocks();
+    G.nitems = (int)(items.size() - (G.items - dit));
+    LL.ngroups = 1;
+    if (items.size() > L.nitems) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyAsync(b + L.params, &p, sizeof(KParams), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.kbufs, kb.data(), kb.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b + L.items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                            ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e;
+}
+
 wdlb_status init_from_stage(wdlb_ctx *ctx, const double *d_n, const double *d_u)
 {
     double n_ref = ctx->opt.n_ref;
@@ -226,6 +311,8 @@ wdlb_status init_from_stage(wdlb_ctx *ctx, const double *d_n, const double *d_u)
     }
     set_reference(ctx, n_ref);
     drop_graphs(ctx);   // kernel parameters changed
+    WDLB_CUDA(ctx, cudaMemcpyAsync(const_cast<KParams *>(ctx->launch.params), &ctx->kp, sizeof(KParams),
+                                   cudaMemcpyHostToDevice, ctx->stream));
     ctx->cur = 0;
     WDLB_CUDA(ctx, cudaMemsetAsync(ctx->dev.status, 0, sizeof(int), ctx->stream));
     WDLB_CUDA(ctx, cudaMemsetAsync(ctx->dev.snap, 0, ctx->N * sizeof(double), ctx->stream));
@@ -241,7 +328,7 @@ wdlb_status init_from_stage(wdlb_ctx *ctx, const double *d_n, const double *d_u)
 wdlb_status step_direct(wdlb_ctx *ctx, int64_t n)
 {
     for (int64_t s = 0; s < n; s++) {
-        cudaError_t e = ctx->L->step(ctx->kp, ctx->dev, ctx->cur, ctx->stream, &ctx->launches);
+        cudaError_t e = ctx->L->batch_step(ctx->launch, ctx->cur, -1, ctx->stream, &ctx->launches);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernels");
         ctx->cur ^= 1;
     }
@@ -258,7 +345,7 @@ wdlb_status ensure_graph(wdlb_ctx *ctx)
     int cc = c;
     cudaError_t err = cudaSuccess;
     for (int s = 0; s < kGraphChunk && err == cudaSuccess; s++) {
-        err = ctx->L->step(ctx->kp, ctx->dev, cc, ctx->stream, &dummy);
+        err = ctx->L->batch_step(ctx->launch, cc, -1, ctx->stream, &dummy);
         cc ^= 1;
     }
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
@@ -310,7 +397,7 @@ wdlb_status wdlb_workspace_size(wdlb_lattice lat, double sigma, int32_t walls, c
     build_shell(sigma, t.shell, &t.wshell);
     long long N = (long long)lat.nx * lat.ny * lat.nz;
     long long Npad = (N + 63) / 64 * 64;
-    *bytes = layout_for(N, Npad, o.storage, (int)t.shell.size() / 3, (int)t.ball.size() / 3).total;
+    *bytes = layout_for(lat, N, Npad, o.storage, (int)t.shell.size() / 3, (int)t.ball.size() / 3).total;
     return WDLB_OK;
 }
 
@@ -347,7 +434,7 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
     ctx->kp.tiled = ctx->L->prepare(ctx->kp) ? 1 : 0;
     set_reference(ctx, o.n_ref > 0 ? o.n_ref : 1.0);
     const int nshell = ctx->kp.nshell, nball = ctx->kp.nball;
-    ctx->lay = layout_for(ctx->N, ctx->Npad, o.storage, nshell, nball);
+    ctx->lay = layout_for(lat, ctx->N, ctx->Npad, o.storage, nshell, nball);
 
     // stream
     if (o.stream) {
@@ -420,6 +507,7 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + L.ball, be.data(), be.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev.status, 0, 16 * sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = upload_step_tables(ctx);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         wdlb_destroy(ctx);
@@ -501,6 +589,8 @@ wdlb_status wdlb_fields(wdlb_ctx *ctx, double *nbar, double *C, double *A, doubl
     double *dn = buf, *dC = buf + N, *dA = buf + 4 * N, *du = buf + 10 * N;
     char *save = reinterpret_cast<char *>(buf + 13 * N);
     cudaError_t e = cudaMemcpyAsync(save, ctx->dev.nu, nu_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    for (int part = 0; part < 2 && e == cudaSuccess; part++)
+        e = ctx->L->batch_step(ctx->launch, ctx->cur, part, ctx->stream, &ctx->launches);
     if (e == cudaSuccess) e = ctx->L->fields(ctx->kp, ctx->dev, ctx->cur, dn, dC, dA, du, ctx->stream, &ctx->launches);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->dev.nu, save, nu_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e == cudaSuccess && nbar) e = cudaMemcpyAsync(nbar, dn, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
@@ -639,7 +729,8 @@ wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3])
     for (int64_t s = 0; s < nsteps && err == cudaSuccess; s++) {
         for (int part = 0; part < 3 && err == cudaSuccess; part++) {
             err = cudaEventRecord(ev[6 * s + 2 * part], ctx->stream);
-            if (err == cudaSuccess) err = ctx->L->step_part(ctx->kp, ctx->dev, ctx->cur, part, ctx->stream, &ctx->launches);
+            if (err == cudaSuccess)
+                err = ctx->L->batch_step(ctx->launch, ctx->cur, part, ctx->stream, &ctx->launches);
             if (err == cudaSuccess) err = cudaEventRecord(ev[6 * s + 2 * part + 1], ctx->stream);
         }
         ctx->cur ^= 1;
@@ -777,7 +868,8 @@ wdlb_status batch_build(wdlb_batch *b)
     const int P = (int)b->slots.size();
     std::vector<KParams> params(P);
     std::vector<char> bufs0(b->L->kbufs_bytes * P, 0), bufs1(b->L->kbufs_bytes * P, 0);
-    std::vector<BatchItem> node_items;
+    std::vector<BatchItem> node_items, ball_items, ball_node_items;
+    size_t ball_smem = 0;
     struct Key {
         int s2, walls, tiled, closure;
         bool operator<(const Key &o) const
@@ -794,6 +886,17 @@ wdlb_status batch_build(wdlb_batch *b)
         b->L->kbufs_fill(c->dev, c->cur ^ 1, bufs1.data() + s * b->L->kbufs_bytes);
         const int N = (int)c->N;
         for (int k = 0; k < (N + 255) / 256; k++) node_items.push_back(BatchItem{s, k, 0, 0});
+        if (c->kp.ball_tiled) {
+            const int bt = kBallTile;
+            const int tx = (c->lat.nx + bt - 1) / bt, ty = (c->lat.ny + bt - 1) / bt, tz = (c->lat.nz + bt - 1) / bt;
+            for (int z = 0; z < tz; z++)
+                for (int y = 0; y < ty; y++)
+                    for (int x = 0; x < tx; x++) ball_items.push_back(BatchItem{s, x, y, z});
+            const size_t tsize = c->opt.storage == WDLB_STORE_F64 ? sizeof(double) : sizeof(float);
+            ball_smem = std::max(ball_smem, ball_tile_smem(c->kp.ball_r, c->kp.nball, tsize));
+        } else {
+            for (int k = 0; k < (N + 255) / 256; k++) ball_node_items.push_back(BatchItem{s, k, 0, 0});
+        }
         Key key{c->kp.tiled ? c->kp.s2 : 0, c->walls, c->kp.tiled, c->kp.closure};
         auto &g = groups[key];
         if (c->kp.tiled) {
@@ -806,7 +909,7 @@ wdlb_status batch_build(wdlb_batch *b)
         }
     }
     if ((int)groups.size() > kMaxBatchGroups) return bfail(b, WDLB_ERR_ARG, "too many kernel variants in one batch");
-    size_t total = node_items.size();
+    size_t total = node_items.size() + ball_items.size() + ball_node_items.size();
     for (auto &g : groups) total += g.second.size();
     if (total > b->items_cap) {
         if (b->d_items) cudaFree(b->d_items);
@@ -824,6 +927,13 @@ wdlb_status batch_build(wdlb_batch *b)
     L.bufs[1] = b->d_bufs[1];
     L.node_items = b->d_items;
     L.n_node_items = (int)node_items.size();
+    L.ball_items = b->d_items + all.size();
+    L.n_ball_items = (int)ball_items.size();
+    L.ball_smem = ball_smem;
+    all.insert(all.end(), ball_items.begin(), ball_items.end());
+    L.ball_node_items = b->d_items + all.size();
+    L.n_ball_node_items = (int)ball_node_items.size();
+    all.insert(all.end(), ball_node_items.begin(), ball_node_items.end());
     L.ngroups = 0;
     for (auto &g : groups) {
         BatchGroup &G = L.groups[L.ngroups++];
@@ -855,7 +965,7 @@ wdlb_status batch_build(wdlb_batch *b)
 wdlb_status batch_step_direct(wdlb_batch *b, int64_t n)
 {
     for (int64_t s = 0; s < n; s++) {
-        cudaError_t e = b->L->batch_step(b->launch, (int)(b->steps_since_build & 1), b->stream, &b->launches);
+        cudaError_t e = b->L->batch_step(b->launch, (int)(b->steps_since_build & 1), -1, b->stream, &b->launches);
         if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch step: %s", cudaGetErrorString(e));
         b->steps_since_build++;
     }
@@ -869,8 +979,8 @@ wdlb_status batch_ensure_graph(wdlb_batch *b)
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return bfail(b, WDLB_ERR_CUDA, "batch capture");
     int64_t count = 0;
-    cudaError_t e = b->L->batch_step(b->launch, 0, b->stream, &count);
-    if (e == cudaSuccess) e = b->L->batch_step(b->launch, 1, b->stream, &count);
+    cudaError_t e = b->L->batch_step(b->launch, 0, -1, b->stream, &count);
+    if (e == cudaSuccess) e = b->L->batch_step(b->launch, 1, -1, b->stream, &count);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);

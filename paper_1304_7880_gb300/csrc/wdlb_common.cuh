@@ -50,6 +50,8 @@ struct KParams {
     int closure, omega_mode, interactions;
     int s2;                  // 2 sigma if it is an integer, else 0 (selects a compiled shell)
     int tiled;               // 1: use the shared-memory tiled shell kernel
+    int ball_r;              // largest |component| of a ball vector (halo of the tiled ball sum)
+    int ball_tiled;          // 1: use the shared-memory tiled ball sum
     double g[3];             // external acceleration
     double omega;            // 1/tau
     double tau;
@@ -64,6 +66,17 @@ struct KParams {
     double ref_ng;           // n_ref g2(n_ref) (NBAR mode)
     double h_pred;           // kappa beta / 6: implicit factor of the field-velocity predictor per unit t
 };
+
+// Tiled ball sum: an 8 x 8 x 8 brick of nodes per block with a halo of
+// ball_r, the brick's n - n_off and the ball's offsets in shared memory.
+constexpr int kBallTile = 8;
+constexpr size_t kBallTileMaxSmem = 48 * 1024;   // no opt-in attribute needed
+
+inline __host__ __device__ size_t ball_tile_smem(int ball_r, int nball, size_t tsize)
+{
+    const size_t side = size_t(kBallTile + 2 * ball_r);
+    return side * side * side * tsize + size_t(nball) * sizeof(int);
+}
 
 // Device buffers of one lattice.  S: storage type of populations; T: compute type.
 template <class S, class T>

@@ -1,14 +1,23 @@
-// Kernels of one WDLB time step (Sec. 5, Numerical results: the five-step
-// algorithm), templated on population storage S, closure CL and geometry
-// (WALLS); the relaxation mode is a runtime branch.  Compute type T = Store<S>::T.
+// Per-block bodies of one WDLB time step (Sec. 5, Numerical results: the
+// five-step algorithm), templated on population storage S, closure CL and
+// geometry (WALLS); the relaxation mode is a runtime branch.  Compute type
+// T = Store<S>::T.  The step kernels that run them (one launch per phase for
+// every lattice of a table) are in wdlb_launch.cu.
 //
-//   k_moments        step 4 of Sec. 5 (Eq. colonna): n, j from f, and the
+//   moments_body     step 4 of Sec. 5 (Eq. colonna): n, j from f, and the
 //                    field velocity v, a lagged linear-implicit predictor of
 //                    the trapezoidal velocity u = j/n + g/2 + C/(2n):
 //                      (1 + H) v = j/n + g/2 + C_prev/(2n) + H v_prev,
 //                      H = kappa (beta/2) t_prev / 3,  t = sum_e w g2 n(r+e).
-//   k_ball           smeared density of Sec. 3 over the lattice ball, stored
-//                    as half packing fraction chi/2 per node.
+//   ball_body,       smeared density of Sec. 3 over the lattice ball, stored
+//   ball_tiled_body  as half packing fraction chi/2 per node (per node, or
+//                    per 8^3 brick through shared memory; same sums).
+//   shell_body       steps 2 + 3 of Sec. 5: the shell sums of Eq. campoc
+//                    (C = n (F^mf + F^viscous)) and Eq. campod (A) with
+//                    du = v(r+e) - v(r), the collision of Eq. SMDB with the
+//                    A-term of Eq. eq:dufty2 (second-order forcing), and push
+//                    streaming with half-way bounce-back (the tiled form for
+//                    sigma 3, 4, 6 is in wdlb_shell_tiled.cuh).
 //
 // Deviation form: nu holds n - n_off and hb holds chi/2 - h_off (h_off the
 // value of n_off), so that the mean-field sum, which cancels down to a
@@ -21,11 +30,6 @@
 // earlier.  The pushes of a step encode with the target's current density,
 // which becomes the target's scale for the next step; the stored values stay
 // small near walls, where n departs far from n_off.
-//   k_shell_collide  steps 2 + 3 of Sec. 5: the shell sums of Eq. campoc
-//                    (C = n (F^mf + F^viscous)) and Eq. campod (A) with
-//                    du = v(r+e) - v(r), the collision of Eq. SMDB with the
-//                    A-term of Eq. eq:dufty2 (second-order forcing), and push
-//                    streaming with half-way bounce-back.
 #pragma once
 
 #include "wdlb_common.cuh"
@@ -182,23 +186,69 @@ __device__ __forceinline__ void ball_body(const KParams &p, const V4<T> *nu, T *
     hb[i] = dh;
 }
 
+// Tiled form of ball_body: one 8 x 8 x 8 brick of nodes per block of 256
+// threads (two nodes per thread, z and z + 4), with n - n_off of the brick
+// and its halo of ball_r, and the ball's offsets within it, in shared memory.
+// Beyond a wall the staged value is -n_off (n = 0).  The ball points are
+// added in table order, so every sum is bitwise the one of ball_body.
 template <class T>
-__global__ void __launch_bounds__(256) k_ball(KParams p, const V4<T> *nu, T *hb, const int4 *ball, int *status)
+__device__ __forceinline__ void ball_tiled_body(const KParams &p, const V4<T> *nu, T *hb, const int4 *ball,
+                                                int *status, int bx, int by, int bz)
 {
-    ball_body<T>(p, nu, hb, ball, status, blockIdx.x);
+    extern __shared__ __align__(16) unsigned char ball_smem[];
+    const int R = p.ball_r, SX = kBallTile + 2 * R, NS = SX * SX * SX;
+    T *sn = reinterpret_cast<T *>(ball_smem);
+    int *so = reinterpret_cast<int *>(ball_smem + size_t(NS) * sizeof(T));
+    for (int m = threadIdx.x; m < p.nball; m += blockDim.x) {
+        const int4 e = ball[m];
+        so[m] = e.x + SX * (e.y + SX * e.z);
+    }
+    const T noff = T(p.n_off);
+    const int x0 = bx * kBallTile, y0 = by * kBallTile, z0 = bz * kBallTile;
+    for (int idx = threadIdx.x; idx < NS; idx += blockDim.x) {
+        const int sx = idx % SX, sy = (idx / SX) % SX, sz = idx / (SX * SX);
+        const int gx = wrap_coord(x0 - R + sx, p.nx), gy = wrap_coord(y0 - R + sy, p.ny);
+        int gz = z0 - R + sz;
+        bool inside = true;
+        if (p.walls)
+            inside = gz >= 0 && gz < p.nz;
+        else
+            gz = wrap_coord(gz, p.nz);
+        sn[idx] = inside ? nu[gx + p.nx * (gy + p.ny * gz)].x : -noff;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tzb = threadIdx.x >> 6;
+    for (int half = 0; half < 2; half++) {
+        const int tz = tzb + 4 * half;
+        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+        if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
+        const int i = x + p.nx * (y + p.ny * z);
+        if (solid_plane(p, z)) {
+            hb[i] = -T(p.h_off);
+            continue;
+        }
+        const int base = (tx + R) + SX * ((ty + R) + SX * (tz + R));
+        T sum = T(0);
+        for (int m = 0; m < p.nball; m++) sum += sn[base + so[m]];
+        T dh = T(p.c_half) * sum;
+        if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
+        hb[i] = dh;
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Pair weights of a (+e, -e) pair of the contact shell.  q = g2(chi_mid) n(r+e)
-// (without the quadrature weight), chi_mid/2 = hb(r) + hb(r+e).  s0 = 1 - h(r)
-// - h_off; dh, dn: deviations of the two neighbours.  Besides q+ and q- it
-// returns q+ - q-, formed from the deviations so that it is accurate relative
+// Pair weights of a (+e, -e) pair of the contact shell.  With
+// q = g2(chi_mid) n(r+e) (without the quadrature weight), chi_mid/2 =
+// hb(r) + hb(r+e), the weights are carried doubled, Q = 2q, which makes the
+// Carnahan-Starling value one multiply-add: 2 g2 = (1 + s)/s^3 with
+// s = 1 - chi_mid (Percus-Yevick: (3 - s)/s^2; closure one: 2).  s0 = 1 - h(r)
+// - h_off; dh, dn: deviations of the two neighbours.  Besides Q+ and Q- it
+// returns Q+ - Q-, formed from the deviations so that it is accurate relative
 // to itself (it is what the mean-field sum accumulates):
-//   q+ - q- = g+ (dn+ - dn-) + (g+ - g-) n-,
-//   CS:  g+ - g- = (dh+ - dh-) [s+^2 + s-^2 + s+ s- (1 + s+ + s-)] / (2 s+^3 s-^3)
-//   PY:  g+ - g- = (dh+ - dh-) [3 (s+ + s-)/2 - s+ s-/2] / (s+^2 s-^2)
-// with s = 1 - chi_mid the argument of g2(chi) = (1 + s)/(2 s^3) (CS) or
-// (3 - s)/(2 s^2) (PY).
+//   Q+ - Q- = G+ (dn+ - dn-) + (G+ - G-) n-,   G = 2 g2,
+//   CS:  G+ - G- = (dh+ - dh-) [s+^2 + s-^2 + s+ s- (1 + s+ + s-)] / (s+^3 s-^3)
+//   PY:  G+ - G- = (dh+ - dh-) [3 (s+ + s-) - s+ s-] / (s+^2 s-^2)
+// (exact divided differences of the closures; s- - s+ = dh+ - dh-).
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ T fast_rcp(T x);
@@ -220,87 +270,91 @@ __device__ __forceinline__ void pair_weights(T s0, T noff, T dhp, T dnp, T dhm, 
 {
     const T np = noff + dnp, nm = noff + dnm;
     if (CL == 2) {
-        qp = np;
-        qm = nm;
-        qd = dnp - dnm;
+        qp = T(2) * np;
+        qm = T(2) * nm;
+        qd = T(2) * (dnp - dnm);
         return;
     }
     const T sp = s0 - dhp, sm = s0 - dhm;
     const T spm = sp * sm;
     T gp, gm, gd;
     if (CL == 0) {
-        const T rp = fast_rcp<T>(sp * sp * sp), rm = fast_rcp<T>(sm * sm * sm);
-        gp = (T(0.5) + T(0.5) * sp) * rp;
-        gm = (T(0.5) + T(0.5) * sm) * rm;
-        gd = (dhp - dhm) * (sp * sp + sm * sm + spm * (T(1) + sp + sm)) * (T(0.5) * rp * rm);
+        const T sp2 = sp * sp, sm2 = sm * sm;
+        const T rp = fast_rcp<T>(sp2 * sp), rm = fast_rcp<T>(sm2 * sm);
+        gp = fma(sp, rp, rp);
+        gm = fma(sm, rm, rm);
+        gd = (dhp - dhm) * (sp2 + sm2 + fma(spm, sp + sm, spm)) * (rp * rm);
     } else {
         const T rp = fast_rcp<T>(sp * sp), rm = fast_rcp<T>(sm * sm);
-        gp = (T(1.5) - T(0.5) * sp) * rp;
-        gm = (T(1.5) - T(0.5) * sm) * rm;
-        gd = (dhp - dhm) * (T(1.5) * (sp + sm) - T(0.5) * spm) * (rp * rm);
+        gp = fma(-sp, rp, T(3) * rp);
+        gm = fma(-sm, rm, T(3) * rm);
+        gd = (dhp - dhm) * fma(T(3), sp + sm, -spm) * (rp * rm);
     }
     qp = gp * np;
     qm = gm * nm;
-    qd = gp * (dnp - dnm) + gd * nm;
+    qd = fma(gp, dnp - dnm, gd * nm);
 }
 
-// q(A) - q(B) for two neighbours A, B of the same node from their deviations:
-// g_A (dn_A - dn_B) + n_B (g_A - g_B), with g_A - g_B as in pair_weights.
-// sA, sB: 1 - chi_mid; rA, rB: 1/sA^3, 1/sB^3 (CS) or 1/sA^2, 1/sB^2 (PY);
-// gA: g2 at A; nB = n_off + dn_B.
-template <int CL, class T>
-__device__ __forceinline__ T q_difference(T dnA, T dhA, T sA, T rA, T gA, T dnB, T dhB, T sB, T rB, T nB)
-{
-    if (CL == 2) return dnA - dnB;
-    const T sAB = sA * sB;
-    const T gd = CL == 0 ? (dhA - dhB) * (sA * sA + sB * sB + sAB * (T(1) + sA + sB)) * (T(0.5) * rA * rB)
-                         : (dhA - dhB) * (T(1.5) * (sA + sB) - T(0.5) * sAB) * (rA * rB);
-    return gA * (dnA - dnB) + gd * nB;
-}
-
-// Contact value g2 from s = 1 - chi_mid, with r = 1/s^3 (CS) or 1/s^2 (PY).
-template <int CL, class T>
-__device__ __forceinline__ T g_from_s(T s, T &r)
-{
-    if (CL == 2) {
-        r = T(1);
-        return T(1);
-    }
-    if (CL == 0) {
-        r = fast_rcp<T>(s * s * s);
-        return (T(0.5) + T(0.5) * s) * r;
-    }
-    r = fast_rcp<T>(s * s);
-    return (T(1.5) - T(0.5) * s) * r;
-}
-
-// Shell-sum accumulators (without the quadrature weight w).
+// Shell-sum accumulators (doubled weights Q = 2q, no quadrature weight w).
+// The velocity sums take the neighbours' velocities v' = v(r+e) directly; the
+// node's own velocity v enters W per pair and S once, in shell_forces:
+//   V    = sum Q khat                                      (F^mf)
+//   W    = sum Q khat (khat . (v' - v))                    (F^viscous)
+//   S_ab = sum Q (khat_b v'_a + khat_a v'_b), diagonal once (A, before the
+//          term - (V_a v_b + V_b v_a) that turns v' into v' - v)
+//   t    = sum Q                                           (predictor)
 template <class T>
 struct ShellAcc {
-    T Vx, Vy, Vz;                       // sum q khat                      (F^mf)
-    T Wx, Wy, Wz;                       // sum q khat (khat . dv)          (F^viscous)
-    T Sxx, Syy, Szz, Sxy, Sxz, Syz;     // sum q (khat_b dv_a + khat_a dv_b), diagonal counted once (A)
-    T t;                                // sum q                           (predictor)
+    T Vx, Vy, Vz;
+    T Wx, Wy, Wz;
+    T Sxx, Syy, Szz, Sxy, Sxz, Syz;
+    T t;
 };
 
-// Add the (+e, -e) pair with unit vector (kx, ky, kz) of +e.  khat(-e) = -khat(+e):
-// V takes q+ - q-, W the sum of the two ends' q dv, S their difference.
+// Add the (+e, -e) pair with unit vector (kx, ky, kz) of +e.  khat(-e) = -khat(+e),
+// so W takes the sum of the two ends' Q (v' - v) and S the difference of
+// their Q v'.
 template <class T>
 __device__ __forceinline__ void accumulate_pair(ShellAcc<T> &a, T kx, T ky, T kz, T qp, T qm, T qd, T vpx, T vpy,
                                                 T vpz, T vmx, T vmy, T vmz, T vx, T vy, T vz)
 {
-    const T px = qp * (vpx - vx), py = qp * (vpy - vy), pz = qp * (vpz - vz);
-    const T mx = qm * (vmx - vx), my = qm * (vmy - vy), mz = qm * (vmz - vz);
-    const T sx = px + mx, sy = py + my, sz = pz + mz;
-    const T dx = px - mx, dy = py - my, dz = pz - mz;
-    a.t += qp + qm;
-    a.Vx += kx * qd; a.Vy += ky * qd; a.Vz += kz * qd;
-    const T ks = kx * sx + ky * sy + kz * sz;
-    a.Wx += kx * ks; a.Wy += ky * ks; a.Wz += kz * ks;
-    a.Sxx += kx * dx; a.Syy += ky * dy; a.Szz += kz * dz;
-    a.Sxy += ky * dx + kx * dy;
-    a.Sxz += kz * dx + kx * dz;
-    a.Syz += kz * dy + ky * dz;
+    const T px = qp * vpx, py = qp * vpy, pz = qp * vpz;
+    const T dx = fma(-qm, vmx, px), dy = fma(-qm, vmy, py), dz = fma(-qm, vmz, pz);
+    const T ex = fma(qm, vmx, px), ey = fma(qm, vmy, py), ez = fma(qm, vmz, pz);
+    const T tq = qp + qm;
+    a.t += tq;
+    const T sx = fma(-tq, vx, ex), sy = fma(-tq, vy, ey), sz = fma(-tq, vz, ez);
+    a.Vx = fma(kx, qd, a.Vx); a.Vy = fma(ky, qd, a.Vy); a.Vz = fma(kz, qd, a.Vz);
+    const T ks = fma(kx, sx, fma(ky, sy, kz * sz));
+    a.Wx = fma(kx, ks, a.Wx); a.Wy = fma(ky, ks, a.Wy); a.Wz = fma(kz, ks, a.Wz);
+    a.Sxx = fma(kx, dx, a.Sxx); a.Syy = fma(ky, dy, a.Syy); a.Szz = fma(kz, dz, a.Szz);
+    a.Sxy = fma(ky, dx, fma(kx, dy, a.Sxy));
+    a.Sxz = fma(kz, dx, fma(kx, dz, a.Sxz));
+    a.Syz = fma(kz, dy, fma(ky, dz, a.Syz));
+}
+
+// Fields of one node from its shell sums: C = n (F^mf + F^viscous) with
+// F^mf = -kT sigma^2 w V and F^viscous = beta w W (Eq. campoc),
+// A = -(kT/5) n sigma^2 w S (Eq. campod, not yet traceless), and
+// t = w sum q for the predictor.  w/2 undoes the doubled weights.
+template <class T>
+__device__ __forceinline__ void shell_forces(const KParams &p, const ShellAcc<T> &a, T n, T vx, T vy, T vz, T &Cx,
+                                             T &Cy, T &Cz, T &Axx, T &Ayy, T &Azz, T &Axy, T &Axz, T &Ayz, T &tsum)
+{
+    const T wh = T(0.5) * T(p.wshell);
+    const T mf = -T(CS2) * T(p.sig2) * wh * n;
+    const T vi = T(p.beta) * wh * n;
+    Cx = mf * a.Vx + vi * a.Wx;
+    Cy = mf * a.Vy + vi * a.Wy;
+    Cz = mf * a.Vz + vi * a.Wz;
+    const T pa = -(T(CS2) / T(5)) * T(p.sig2) * n * wh;
+    Axx = T(2) * pa * (a.Sxx - a.Vx * vx);
+    Ayy = T(2) * pa * (a.Syy - a.Vy * vy);
+    Azz = T(2) * pa * (a.Szz - a.Vz * vz);
+    Axy = pa * (a.Sxy - (a.Vy * vx + a.Vx * vy));
+    Axz = pa * (a.Sxz - (a.Vz * vx + a.Vx * vz));
+    Ayz = pa * (a.Syz - (a.Vz * vy + a.Vy * vz));
+    tsum = a.t * wh;
 }
 
 // ---------------------------------------------------------------------------
@@ -477,16 +531,7 @@ __device__ __forceinline__ void shell_body(const KParams &p, const KBufs<S, type
     if (p.interactions) {
         ShellAcc<T> a = {};
         shell_sums_generic<CL, WALLS, T>(p, b.nu, b.hb, b.shell_e, b.shell_k, x, y, z, hr, vx, vy, vz, a);
-        const T w = T(p.wshell);
-        const T mf = -T(CS2) * T(p.sig2) * w * n;
-        const T vi = T(p.beta) * w * n;
-        Cx = mf * a.Vx + vi * a.Wx;
-        Cy = mf * a.Vy + vi * a.Wy;
-        Cz = mf * a.Vz + vi * a.Wz;
-        const T pa = -(T(CS2) / T(5)) * T(p.sig2) * n * w;
-        Axx = T(2) * pa * a.Sxx; Ayy = T(2) * pa * a.Syy; Azz = T(2) * pa * a.Szz;
-        Axy = pa * a.Sxy; Axz = pa * a.Sxz; Ayz = pa * a.Syz;
-        tsum = a.t * w;
+        shell_forces<T>(p, a, n, vx, vy, vz, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum);
     }
     collide_push<S, CL, WALLS, FIELDS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
                                        [&](int, int dst) { return b.nu[dst].x; });
@@ -566,14 +611,24 @@ static __global__ void __launch_bounds__(256) k_stats(KParams p, const double *n
 
 static __global__ void k_stats_final(const double *partial, int nblocks, double *out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    // one warp: lane l takes blocks l, l + 32, ...; then a fixed shuffle tree
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     double r[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < nblocks; b++) {
+    for (int b = threadIdx.x; b < nblocks; b += 32) {
         r[0] += partial[b * 6 + 0]; r[1] += partial[b * 6 + 1]; r[2] += partial[b * 6 + 2];
         r[3] = fmax(r[3], partial[b * 6 + 3]); r[4] = fmax(r[4], partial[b * 6 + 4]);
         r[5] += partial[b * 6 + 5];
     }
-    for (int k = 0; k < 6; k++) out[k] = r[k];
+    for (int off = 16; off > 0; off >>= 1) {
+        r[0] += __shfl_down_sync(0xffffffffu, r[0], off);
+        r[1] += __shfl_down_sync(0xffffffffu, r[1], off);
+        r[2] += __shfl_down_sync(0xffffffffu, r[2], off);
+        r[3] = fmax(r[3], __shfl_down_sync(0xffffffffu, r[3], off));
+        r[4] = fmax(r[4], __shfl_down_sync(0xffffffffu, r[4], off));
+        r[5] += __shfl_down_sync(0xffffffffu, r[5], off);
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; k++) out[k] = r[k];
 }
 
 // FP64 sum of the initial density over fluid nodes (for the default n_ref).

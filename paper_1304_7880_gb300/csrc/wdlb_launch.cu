@@ -26,34 +26,52 @@ constexpr int kThreads = 256;
 
 inline int blocks_for(int n) { return (n + kThreads - 1) / kThreads; }
 
-// ---- multi-lattice kernels: one launch for all slots, same kernel bodies ----
-__global__ void __launch_bounds__(256) k_moments_batch(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
+// ---- step kernels: one launch for all slots of a table ----
+// Every block copies its slot's parameters and buffer pointers into registers
+// and runs the per-block body.  A lattice stepped alone runs these kernels
+// through a one-slot table.
+__global__ void __launch_bounds__(256) k_step_moments(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
-    moments_body<S, false>(P[w.slot], B[w.slot], w.bx, nullptr, nullptr);
+    const KParams p = P[w.slot];
+    const KBufs<S, T> b = B[w.slot];
+    moments_body<S, false>(p, b, w.bx, nullptr, nullptr);
 }
 
-__global__ void __launch_bounds__(256) k_ball_batch(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
+__global__ void __launch_bounds__(256) k_step_ball(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
-    const KBufs<S, T> &b = B[w.slot];
-    ball_body<T>(P[w.slot], b.nu, b.hb, b.ball, b.status, w.bx);
+    const KParams p = P[w.slot];
+    const KBufs<S, T> b = B[w.slot];
+    ball_body<T>(p, b.nu, b.hb, b.ball, b.status, w.bx);
+}
+
+__global__ void __launch_bounds__(256) k_step_ball_tiled(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
+{
+    const BatchItem w = it[blockIdx.x];
+    const KParams p = P[w.slot];
+    const KBufs<S, T> b = B[w.slot];
+    ball_tiled_body<T>(p, b.nu, b.hb, b.ball, b.status, w.bx, w.by, w.bz);
 }
 
 template <int CL, bool WALLS>
-__global__ void __launch_bounds__(256) k_shell_batch(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
+__global__ void __launch_bounds__(256) k_step_shell(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
-    shell_body<S, CL, WALLS, false>(P[w.slot], B[w.slot], w.bx);
+    const KParams p = P[w.slot];
+    const KBufs<S, T> b = B[w.slot];
+    shell_body<S, CL, WALLS, false>(p, b, w.bx);
 }
 
 #if WDLB_STORAGE != 0
 template <int S2, bool WALLS>
-__global__ void __launch_bounds__(tiled::THREADS, 2) k_tiled_batch(const KParams *P, const KBufs<S, float> *B,
-                                                                  const BatchItem *it)
+__global__ void __launch_bounds__(tiled::threads_for(S2), tiled::blocks_per_sm(S2))
+    k_step_shell_tiled(const KParams *P, const KBufs<S, float> *B, const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
-    tiled::tiled_body<S, S2, 0, WALLS, false>(P[w.slot], B[w.slot], w.bx, w.by, w.bz);
+    const KParams p = P[w.slot];
+    const KBufs<S, float> b = B[w.slot];
+    tiled::tiled_body<S, S2, 0, WALLS, false>(p, b, w.bx, w.by, w.bz);
 }
 #endif
 
@@ -75,54 +93,20 @@ KBufs<S, T> typed(const DevBufs &d, int cur)
     return b;
 }
 
-template <int CL, bool WALLS, bool FIELDS>
-void launch_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
+template <int CL, bool WALLS>
+void launch_fields_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
 {
-    k_shell_collide<S, CL, WALLS, FIELDS><<<blocks_for(p.N), kThreads, 0, st>>>(p, b);
+    k_shell_collide<S, CL, WALLS, true><<<blocks_for(p.N), kThreads, 0, st>>>(p, b);
 }
 
 #if WDLB_STORAGE != 0
 // The tiled kernel is compiled for the Carnahan-Starling closure (the default)
-// and sigma in {3, 4, 6}; other closures and sigmas use k_shell_collide.
+// and sigma in {3, 4, 6}; other closures and sigmas use the generic kernel.
 template <int S2, bool WALLS>
 cudaError_t tiled_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(tiled::k_shell_tiled<S, S2, 0, WALLS, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiled::smem_bytes<S2>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tiled_batch<S2, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_step_shell_tiled<S2, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tiled::smem_bytes<S2>());
-}
-
-template <int S2, bool WALLS>
-void launch_tiled(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
-{
-    dim3 grid((p.nx + tiled::TX - 1) / tiled::TX, (p.ny + tiled::TY - 1) / tiled::TY,
-              (p.nz + tiled::TZ - 1) / tiled::TZ);
-    tiled::k_shell_tiled<S, S2, 0, WALLS, false><<<grid, tiled::THREADS, tiled::smem_bytes<S2>(), st>>>(p, b);
-}
-
-template <int S2>
-void tiled_s2(const KParams &p, const KBufs<S, T> *b, cudaStream_t st, cudaError_t *attr)
-{
-    if (p.walls) {
-        if (attr) *attr = tiled_attr<S2, true>();
-        else launch_tiled<S2, true>(p, *b, st);
-    } else {
-        if (attr) *attr = tiled_attr<S2, false>();
-        else launch_tiled<S2, false>(p, *b, st);
-    }
-}
-
-// attr != nullptr: set kernel attributes instead of launching
-void dispatch_tiled(const KParams &p, const KBufs<S, T> *b, cudaStream_t st, cudaError_t *attr)
-{
-    switch (p.s2) {
-    case 6: tiled_s2<6>(p, b, st, attr); break;
-    case 8: tiled_s2<8>(p, b, st, attr); break;
-    case 12: tiled_s2<12>(p, b, st, attr); break;
-    default: break;
-    }
 }
 #endif
 
@@ -141,36 +125,15 @@ bool do_prepare(const KParams &p)
     if (!tiled_eligible(p)) return false;
 #if WDLB_STORAGE != 0
     cudaError_t e = cudaSuccess;
-    dispatch_tiled(p, nullptr, nullptr, &e);
+    switch (p.s2) {
+    case 6: e = p.walls ? tiled_attr<6, true>() : tiled_attr<6, false>(); break;
+    case 8: e = p.walls ? tiled_attr<8, true>() : tiled_attr<8, false>(); break;
+    default: e = p.walls ? tiled_attr<12, true>() : tiled_attr<12, false>(); break;
+    }
     return e == cudaSuccess;
 #else
     return false;
 #endif
-}
-
-template <bool FIELDS>
-void dispatch_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
-{
-#if WDLB_STORAGE != 0
-    if (!FIELDS && p.tiled) {
-        dispatch_tiled(p, &b, st, nullptr);
-        return;
-    }
-#endif
-#define WDLB_CASE(CL, W)                                \
-    if (p.closure == CL && (p.walls != 0) == W) {       \
-        launch_shell<CL, W, FIELDS>(p, b, st);          \
-        return;                                         \
-    }
-    WDLB_CASE(0, true) WDLB_CASE(0, false) WDLB_CASE(1, true) WDLB_CASE(1, false) WDLB_CASE(2, true)
-    WDLB_CASE(2, false)
-#undef WDLB_CASE
-}
-
-void moments_ball(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
-{
-    k_moments<S, false><<<blocks_for(p.N), kThreads, 0, st>>>(p, b, nullptr, nullptr);
-    k_ball<T><<<blocks_for(p.N), kThreads, 0, st>>>(p, b.nu, b.hb, b.ball, b.status);
 }
 
 cudaError_t do_init(const KParams &p, const DevBufs &d, int cur, const double *d_n, const double *d_u,
@@ -178,28 +141,6 @@ cudaError_t do_init(const KParams &p, const DevBufs &d, int cur, const double *d
 {
     KBufs<S, T> b = typed(d, cur ^ 1);   // f_out = buffer `cur`
     k_init<S><<<blocks_for(p.N), kThreads, 0, st>>>(p, b, d_n, d_u);
-    *launches += 1;
-    return cudaGetLastError();
-}
-
-cudaError_t do_step(const KParams &p, const DevBufs &d, int cur, cudaStream_t st, int64_t *launches)
-{
-    KBufs<S, T> b = typed(d, cur);
-    moments_ball(p, b, st);
-    dispatch_shell<false>(p, b, st);
-    *launches += 3;
-    return cudaGetLastError();
-}
-
-cudaError_t do_step_part(const KParams &p, const DevBufs &d, int cur, int part, cudaStream_t st, int64_t *launches)
-{
-    KBufs<S, T> b = typed(d, cur);
-    if (part == 0)
-        k_moments<S, false><<<blocks_for(p.N), kThreads, 0, st>>>(p, b, nullptr, nullptr);
-    else if (part == 1)
-        k_ball<T><<<blocks_for(p.N), kThreads, 0, st>>>(p, b.nu, b.hb, b.ball, b.status);
-    else
-        dispatch_shell<false>(p, b, st);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -212,10 +153,16 @@ cudaError_t do_fields(const KParams &p, const DevBufs &d, int cur, double *nbar,
     b.out_C = C;
     b.out_A = A;
     b.out_u = u;
-    moments_ball(p, b, st);
-    dispatch_shell<true>(p, b, st);
-    *launches += 3;
-    return cudaGetLastError();
+#define WDLB_CASE(CL, W)                                \
+    if (p.closure == CL && (p.walls != 0) == W) {       \
+        launch_fields_shell<CL, W>(p, b, st);           \
+        *launches += 1;                                 \
+        return cudaGetLastError();                      \
+    }
+    WDLB_CASE(0, true) WDLB_CASE(0, false) WDLB_CASE(1, true) WDLB_CASE(1, false) WDLB_CASE(2, true)
+    WDLB_CASE(2, false)
+#undef WDLB_CASE
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t do_moments(const KParams &p, const DevBufs &d, int cur, double *d_n, double *d_u, cudaStream_t st,
@@ -254,14 +201,24 @@ void kbufs_fill(const DevBufs &d, int cur, void *out)
     std::memcpy(out, &b, sizeof(b));
 }
 
-cudaError_t do_batch_step(const BatchLaunch &L, int parity, cudaStream_t st, int64_t *launches)
+cudaError_t do_batch_step(const BatchLaunch &L, int parity, int part, cudaStream_t st, int64_t *launches)
 {
     const KBufs<S, T> *B = static_cast<const KBufs<S, T> *>(L.bufs[parity & 1]);
-    if (L.n_node_items > 0) {
-        k_moments_batch<<<L.n_node_items, kThreads, 0, st>>>(L.params, B, L.node_items);
-        k_ball_batch<<<L.n_node_items, kThreads, 0, st>>>(L.params, B, L.node_items);
-        *launches += 2;
+    if ((part < 0 || part == 0) && L.n_node_items > 0) {
+        k_step_moments<<<L.n_node_items, kThreads, 0, st>>>(L.params, B, L.node_items);
+        *launches += 1;
     }
+    if (part < 0 || part == 1) {
+        if (L.n_ball_items > 0) {
+            k_step_ball_tiled<<<L.n_ball_items, kThreads, L.ball_smem, st>>>(L.params, B, L.ball_items);
+            *launches += 1;
+        }
+        if (L.n_ball_node_items > 0) {
+            k_step_ball<<<L.n_ball_node_items, kThreads, 0, st>>>(L.params, B, L.ball_node_items);
+            *launches += 1;
+        }
+    }
+    if (part >= 0 && part != 2) return cudaGetLastError();
     for (int g = 0; g < L.ngroups; g++) {
         const BatchGroup &G = L.groups[g];
         if (G.nitems == 0) continue;
@@ -269,7 +226,8 @@ cudaError_t do_batch_step(const BatchLaunch &L, int parity, cudaStream_t st, int
         if (G.tiled) {
             const size_t sm = G.s2 == 6 ? tiled::smem_bytes<6>() : (G.s2 == 8 ? tiled::smem_bytes<8>()
                                                                                : tiled::smem_bytes<12>());
-#define WDLB_TB(S2V, WV) k_tiled_batch<S2V, WV><<<G.nitems, tiled::THREADS, sm, st>>>(L.params, B, G.items)
+#define WDLB_TB(S2V, WV) \
+    k_step_shell_tiled<S2V, WV><<<G.nitems, tiled::threads_for(S2V), sm, st>>>(L.params, B, G.items)
             if (G.s2 == 6) { if (G.walls) WDLB_TB(6, true); else WDLB_TB(6, false); }
             else if (G.s2 == 8) { if (G.walls) WDLB_TB(8, true); else WDLB_TB(8, false); }
             else { if (G.walls) WDLB_TB(12, true); else WDLB_TB(12, false); }
@@ -278,7 +236,7 @@ cudaError_t do_batch_step(const BatchLaunch &L, int parity, cudaStream_t st, int
             continue;
         }
 #endif
-#define WDLB_SB(CLV, WV) k_shell_batch<CLV, WV><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items)
+#define WDLB_SB(CLV, WV) k_step_shell<CLV, WV><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items)
         if (G.closure == 0) { if (G.walls) WDLB_SB(0, true); else WDLB_SB(0, false); }
         else if (G.closure == 1) { if (G.walls) WDLB_SB(1, true); else WDLB_SB(1, false); }
         else { if (G.walls) WDLB_SB(2, true); else WDLB_SB(2, false); }
@@ -288,7 +246,9 @@ cudaError_t do_batch_step(const BatchLaunch &L, int parity, cudaStream_t st, int
     return cudaGetLastError();
 }
 
-const Launchers kL = {do_prepare, sizeof(KBufs<S, T>), kbufs_fill, do_batch_step, do_init, do_step, do_step_part, do_fields, do_moments, do_population, do_stats};
+static_assert(sizeof(KBufs<S, T>) <= kKBufsMaxBytes, "KBufs larger than its table slot");
+const Launchers kL = {do_prepare, sizeof(KBufs<S, T>), kbufs_fill, do_batch_step, do_init,
+                      do_fields,  do_moments,         do_population, do_stats};
 
 }  // namespace
 

@@ -52,28 +52,46 @@ constexpr int kMaxBatchGroups = 16;
 struct BatchLaunch {
     const KParams *params;
     const void *bufs[2];
-    const BatchItem *node_items;
+    const BatchItem *node_items;      // blocks of 256 nodes of every slot (moments)
     int n_node_items;
+    const BatchItem *ball_items;      // 8^3 bricks of the slots with a tiled ball sum
+    int n_ball_items;
+    size_t ball_smem;                 // largest tiled ball shared memory among them
+    const BatchItem *ball_node_items; // blocks of 256 nodes of the other slots
+    int n_ball_node_items;
     BatchGroup groups[kMaxBatchGroups];
     int ngroups;
 };
+
+constexpr size_t kKBufsMaxBytes = 256;   // room for one KBufs of any storage type in a table
+
+// Work items of one lattice stepped alone (a one-slot table): blocks of 256
+// nodes, 8^3 bricks, and the shell items (bricks when tiled, else blocks).
+inline int node_blocks(const KParams &p) { return (p.N + 255) / 256; }
+inline int brick_count(const KParams &p) { return ((p.nx + 7) / 8) * ((p.ny + 7) / 8) * ((p.nz + 7) / 8); }
+inline size_t single_items(const KParams &p)
+{
+    const int nb = node_blocks(p), nt = brick_count(p);
+    return size_t(nb) + 2 * size_t(nb > nt ? nb : nt);
+}
 
 struct Launchers {
     // per-context preparation outside any stream capture (kernel attributes);
     // returns whether the tiled shell kernel can serve these parameters
     bool (*prepare)(const KParams &);
-    // multi-lattice step: size of one KBufs, writing it for input buffer `cur`,
-    // and one time step of every slot in the tables (input buffers of parity p)
+    // step tables: size of one KBufs, writing it for input buffer `cur`
     size_t kbufs_bytes;
     void (*kbufs_fill)(const DevBufs &, int cur, void *out);
-    cudaError_t (*batch_step)(const BatchLaunch &, int parity, cudaStream_t, int64_t *launches);
+    // one time step of every slot in the tables (input buffers of parity p);
+    // part -1: all three kernels, 0: moments, 1: smeared density, 2: shell
+    // sums + collision + streaming.  A lattice stepped alone uses the same
+    // kernels through a one-slot table, so it steps bit-identically alone and
+    // in a batch.
+    cudaError_t (*batch_step)(const BatchLaunch &, int parity, int part, cudaStream_t, int64_t *launches);
     cudaError_t (*init)(const KParams &, const DevBufs &, int cur, const double *d_n, const double *d_u,
                         cudaStream_t, int64_t *launches);
-    // one time step from buffer `cur` into `cur ^ 1`
-    cudaError_t (*step)(const KParams &, const DevBufs &, int cur, cudaStream_t, int64_t *launches);
-    // one kernel of a time step from buffer `cur`: part 0 moments, 1 ball, 2 shell + collide + stream
-    cudaError_t (*step_part)(const KParams &, const DevBufs &, int cur, int part, cudaStream_t, int64_t *launches);
-    // fields of the state in buffer `cur` (moments, ball and the shell sums; no streaming)
+    // shell fields of the state in buffer `cur` after its moments and smeared
+    // density were updated by batch_step parts 0 and 1 (no streaming)
     cudaError_t (*fields)(const KParams &, const DevBufs &, int cur, double *nbar, double *C, double *A,
                           double *u, cudaStream_t, int64_t *launches);
     // moments of the state in buffer `cur` into FP64 device arrays (either may be NULL)

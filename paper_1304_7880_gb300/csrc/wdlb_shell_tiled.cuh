@@ -2,8 +2,11 @@
 // Sec. 5), in FP32, with the field tile and its shell halo staged in shared
 // memory.
 //
-// Block: 256 threads, an 8 x 8 x 8 brick of output nodes (two per thread, z
-// and z + 4).  Shared memory holds (8 + 2R)^3 nodes of (n - n_off, v_x, v_y,
+// Block: an 8 x 8 x 8 brick of output nodes; 256 threads with two nodes each
+// (z and z + 4), two blocks per SM, where the staged tile is small enough
+// (sigma 3, 4); 512 threads with one node each, one block per SM, for
+// sigma 6, whose tile takes 160 KB of shared memory (16 warps per SM instead
+// of 8 hide more of the pair loop's latency).  Shared memory holds (8 + 2R)^3 nodes of (n - n_off, v_x, v_y,
 // v_z) and hb - h_off, R = floor(sigma + 1/2), with periodic wrap in x, y (and
 // z without walls) and n = 0 beyond the walls, so the shell loop needs no
 // bounds checks: a solid or missing neighbour has n = 0 and adds nothing.
@@ -19,7 +22,10 @@
 namespace wdlb {
 namespace tiled {
 
-constexpr int TX = 8, TY = 8, TZ = 8, THREADS = 256;
+constexpr int TX = 8, TY = 8, TZ = 8;
+
+constexpr int threads_for(int S2) { return S2 >= 12 ? 512 : 256; }
+constexpr int blocks_per_sm(int S2) { return S2 >= 12 ? 1 : 2; }
 
 constexpr int shell_radius(int S2) { return (S2 + 1) / 2; }
 
@@ -50,6 +56,8 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
     constexpr int SX = TX + 2 * R, SY = TY + 2 * R, SZ = TZ + 2 * R;
     constexpr int NS = SX * SY * SZ;
     constexpr int NPAIR = shell_count(S2) / 2;
+    constexpr int NT = threads_for(S2);
+    constexpr int ZSTEP = NT / (TX * TY);     // z rows covered by one pass of the block
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *sm4 = reinterpret_cast<float4 *>(smem_raw);
     float4 *smt = reinterpret_cast<float4 *>(smem_raw + sizeof(float4) * NS);
@@ -59,14 +67,14 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
     const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
 
     // shell pairs: +e is entry 2m of the library's table (-e is 2m + 1)
-    for (int m = threadIdx.x; m < NPAIR; m += THREADS) {
+    for (int m = threadIdx.x; m < NPAIR; m += NT) {
         const int4 e = b.shell_e[2 * m];
         const V4<float> k = b.shell_k[2 * m];
         smt[m] = make_float4(k.x, k.y, k.z, __int_as_float(e.x + SX * (e.y + SY * e.z)));
     }
     // the field tile with its halo
     const float noff = float(p.n_off), hoff = float(p.h_off);
-    for (int idx = threadIdx.x; idx < NS; idx += THREADS) {
+    for (int idx = threadIdx.x; idx < NS; idx += NT) {
         const int sx = idx % SX, sy = (idx / SX) % SY, sz = idx / (SX * SY);
         int gx = x0 - R + sx, gy = y0 - R + sy, gz = z0 - R + sz;
         gx = ((gx % nx) + nx) % nx;
@@ -91,8 +99,8 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
 
     const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tzb = threadIdx.x >> 6;
 #pragma unroll 1
-    for (int half = 0; half < 2; half++) {
-        const int tz = tzb + 4 * half;
+    for (int half = 0; half < TZ / ZSTEP; half++) {
+        const int tz = tzb + ZSTEP * half;
         const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
         if (x >= nx || y >= ny || z >= nz) continue;
         if (WALLS && (z == 0 || z == nz - 1)) continue;
@@ -119,28 +127,13 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
                 accumulate_pair<float>(a, t.x, t.y, t.z, qp, qm, qd, np.y, np.z, np.w, nm.y, nm.z, nm.w, me.y,
                                        me.z, me.w);
             }
-            const float w = float(p.wshell);
-            const float n = noff + me.x;
-            const float mf = -float(CS2) * float(p.sig2) * w * n;
-            const float vi = float(p.beta) * w * n;
-            Cx = mf * a.Vx + vi * a.Wx;
-            Cy = mf * a.Vy + vi * a.Wy;
-            Cz = mf * a.Vz + vi * a.Wz;
-            const float pa = -(float(CS2) / 5.f) * float(p.sig2) * n * w;
-            Axx = 2.f * pa * a.Sxx; Ayy = 2.f * pa * a.Syy; Azz = 2.f * pa * a.Szz;
-            Axy = pa * a.Sxy; Axz = pa * a.Sxz; Ayz = pa * a.Syz;
-            tsum = a.t * w;
+            shell_forces<float>(p, a, noff + me.x, me.y, me.z, me.w, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz,
+                                tsum);
         }
         collide_push<S, CL, WALLS, FIELDS>(
             p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
             [&](int q, int) { return sm4[base + cx_of(q) + SX * (cy_of(q) + SY * cz_of(q))].x; });
     }
-}
-
-template <class S, int S2, int CL, bool WALLS, bool FIELDS>
-__global__ void __launch_bounds__(THREADS, 2) k_shell_tiled(KParams p, KBufs<S, float> b)
-{
-    tiled_body<S, S2, CL, WALLS, FIELDS>(p, b, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace tiled

@@ -143,21 +143,12 @@ __global__ void __launch_bounds__(256) k_static_fields(KParams p0, StaticBufs s,
     const V4<float> me = s.nu[i];
     ShellAcc<float> a = {};
     shell_sums_generic<CL, WALLS, float>(p, s.nu, s.hb, s.shell_e, s.shell_k, x, y, z, hr, me.y, me.z, me.w, a);
-    const float w = float(p.wshell);
-    const float n = float(p.n_off) + me.x;
-    const float mf = -float(CS2) * float(p.sig2) * w * n;
-    const float vi = float(p.beta) * w * n;
-    const float pa = -(float(CS2) / 5.f) * float(p.sig2) * n * w;
+    float C[3], A[6], t;
+    shell_forces<float>(p, a, float(p.n_off) + me.x, me.y, me.z, me.w, C[0], C[1], C[2], A[0], A[1], A[2], A[3], A[4],
+                        A[5], t);
     if (d_nbar) d_nbar[i] = double(hr) * 2.0 / p.chi_of_n;
-    d_C[i] = mf * a.Vx + vi * a.Wx;
-    d_C[N + i] = mf * a.Vy + vi * a.Wy;
-    d_C[2 * N + i] = mf * a.Vz + vi * a.Wz;
-    d_A[i] = 2.f * pa * a.Sxx;
-    d_A[N + i] = 2.f * pa * a.Syy;
-    d_A[2 * N + i] = 2.f * pa * a.Szz;
-    d_A[3 * N + i] = pa * a.Sxy;
-    d_A[4 * N + i] = pa * a.Sxz;
-    d_A[5 * N + i] = pa * a.Syz;
+    for (int c = 0; c < 3; c++) d_C[c * N + i] = C[c];
+    for (int c = 0; c < 6; c++) d_A[c * N + i] = A[c];
 }
 
 template <int CL>
