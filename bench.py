@@ -229,6 +229,35 @@ SERVE_WORKLOAD = ("slit Poiseuille requests: sigma in {3,4,6}, H/sigma lognormal
                   "admission budget, FIFO admission, at most 48 pores stepped together")
 
 
+def run_single_pore(w, synth, np, count=4, tol=1e-8):
+    """The first `count` requests of the serving stream solved one at a time,
+    alone on the GPU, on the plain FP64 path and on the FP32 path (same
+    kernels as the batch), to the same steady-state tolerance; solves/s of
+    each and the largest relative difference of their pore fluxes."""
+    reqs = synth.serving_requests(200.0, 5.0)[:count]
+    out = {}
+    flux = {}
+    for storage in ("f64", "f32"):
+        t_total, steps_total = 0.0, 0
+        for k, (_, q, seed) in enumerate(reqs):
+            pp, n, _ = synth.slit_poiseuille(q["nx"], q["ny"], q["nz"], q["n_star"], q["sigma"], q["tau"], q["gx"],
+                                             seed)
+            ctx = w.wdlb_create((q["nx"], q["ny"], q["nz"]), q["sigma"], True, q["tau"], pp["g"], storage=storage)
+            w.wdlb_init_fields(ctx, n)
+            t0 = time.perf_counter()
+            steps, _ = w.wdlb_run_steady(ctx, tol, 100, 10 ** 6)
+            t_total += time.perf_counter() - t0
+            steps_total += steps
+            flux[(storage, k)] = w.wdlb_pore_average(ctx)["flux_x"]
+            w.wdlb_destroy(ctx)
+        out[storage] = {"solves_per_s": count / t_total, "seconds": t_total, "time_steps": steps_total}
+    out["flux_rel_diff_max"] = max(abs(flux[("f32", k)] - flux[("f64", k)]) / abs(flux[("f64", k)])
+                                   for k in range(count))
+    out["sample"] = ("first %d requests of the serving stream, solved one at a time to relative pore-flux "
+                     "change < %g per step" % (count, tol))
+    return out
+
+
 def run_serving_pair(w, synth, np):
     """Overload at 200 requests/s measures the capacity (completed solves/s);
     a second run offered 70 % of that capacity gives latencies with a bounded
@@ -238,6 +267,7 @@ def run_serving_pair(w, synth, np):
     out = {"workload": SERVE_WORKLOAD, "overload": over, "capacity_solves_per_s": cap}
     if cap > 0:
         out["at_70pct_capacity"] = run_serving(w, synth, np, rate=0.7 * cap, window_s=20.0, drain_s=20.0)
+    out["single_pore"] = run_single_pore(w, synth, np)
     return out
 
 

@@ -86,7 +86,17 @@ typedef struct {
     uint64_t workspace_bytes; /* size of workspace                                   */
     void *stream;             /* cudaStream_t for all work; NULL: the library creates
                                  (and destroys) its own non-blocking stream          */
+    int32_t tile;             /* shape of the shared-memory tiled shell kernel (FP32
+                                 and FP16 storage, CS closure, sigma 3, 4 or 6):
+                                 -1 (default) chosen by the autotuner, 0 8x8x8 bricks
+                                 on 256 threads, 1 8x8x8 on 512 threads, 2 8x8x4 on
+                                 256 threads (WDLB_TILE_*)                          */
+    int32_t autotune;         /* with tile = -1: 1 (default) time the tile variants on
+                                 a scratch lattice the first time a (storage, sigma,
+                                 walls, nz) key is seen; 0 use the built-in table    */
 } wdlb_options;
+
+enum { WDLB_TILE_AUTO = -1, WDLB_TILE_8x8x8 = 0, WDLB_TILE_8x8x8_WIDE = 1, WDLB_TILE_8x8x4 = 2 };
 
 /* Fill *opt with the defaults above.  opt must not be NULL. */
 void wdlb_default_options(wdlb_options *opt);
@@ -186,10 +196,39 @@ wdlb_status wdlb_stencil(double sigma, int32_t which, int32_t *vecs, int32_t cap
  * streaming.  Synchronous. */
 wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3]);
 
+/* ---- Tile autotuner (no counterpart in the paper: a launch-shape choice) --
+ *
+ * The tiled shell kernel comes in three shapes (WDLB_TILE_*).  Which one is
+ * fastest depends on sigma (shared memory per block, hence blocks per SM) and
+ * on nz (z padding of the bricks in thin slits).  Contexts created with
+ * tile = -1 take the shape from a process-wide table keyed by (storage,
+ * sigma, walls, nz).  A missing key is filled by timing every shape on a
+ * scratch lattice of that key (nz as given, a square cross-section of about
+ * 2^20 / nz nodes so that the kernel fills the GPU as a batch does; uniform
+ * density; six steps after two warm-up steps) when autotune = 1, else from a
+ * built-in table.  Every shape computes the same arithmetic per node; alone
+ * and batched lattices of one key share the table entry, so they run the
+ * same kernel.  Thread-safe; the table lives until wdlb_autotune_reset. */
+
+/* Time every tile shape for this key now (replacing its table entry).
+ * *best: the fastest shape; ms[3]: milliseconds per time step of each shape's
+ * shell kernel (NaN for a shape that cannot run); either may be NULL.
+ * WDLB_ERR_ARG if the tiled kernel does not apply to these arguments. */
+wdlb_status wdlb_autotune(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_options *opt,
+                          int32_t *best, double ms[3]);
+
+/* The shell kernel a context runs: *tiled 1 for the tiled kernel (then
+ * *tile is its shape), 0 for the per-node kernel (*tile = -1). */
+wdlb_status wdlb_tile_info(const wdlb_ctx *ctx, int32_t *tiled, int32_t *tile);
+
+/* Forget every autotuned entry (later contexts probe again). */
+void wdlb_autotune_reset(void);
+
 /* ---- Batches of independent lattices (continuous batching) --------------
  * Many pores of different sizes stepped together: each phase of a time step
  * is one kernel launch for all pores of the batch (one shell launch per group
- * of pores with the same sigma and geometry), replayed from a CUDA graph.
+ * of pores with the same sigma, geometry and tile shape), replayed from a
+ * CUDA graph.
  * The kernels are those of the single-lattice path, so a pore's result is the
  * same alone and in a batch.  Pores are admitted by device-memory footprint
  * into a pool of fixed size and removed when done; admission, removal and

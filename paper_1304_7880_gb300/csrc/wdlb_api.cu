@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <cmath>
 #include <cstdarg>
@@ -52,7 +53,7 @@ int compute_bytes(int storage) { return storage == WDLB_STORE_F64 ? 8 : 4; }
 size_t step_items(wdlb_lattice lat, long long N)
 {
     const size_t nb = size_t((N + 255) / 256);
-    const size_t nt = size_t((lat.nx + 7) / 8) * size_t((lat.ny + 7) / 8) * size_t((lat.nz + 7) / 8);
+    const size_t nt = size_t((lat.nx + 7) / 8) * size_t((lat.ny + 7) / 8) * size_t((lat.nz + 3) / 4);
     return nb + 2 * std::max(nb, nt);
 }
 
@@ -167,6 +168,7 @@ wdlb_status validate(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_o
         if (opt->omega_mode < 0 || opt->omega_mode > 1) return WDLB_ERR_ARG;
         if (opt->storage < 0 || opt->storage > 2) return WDLB_ERR_ARG;
         if (!(opt->n_ref >= 0.0) || !std::isfinite(opt->k_cross)) return WDLB_ERR_ARG;
+        if (opt->tile < -1 || opt->tile > 2 || opt->autotune < 0 || opt->autotune > 1) return WDLB_ERR_ARG;
     }
     return WDLB_OK;
 }
@@ -245,8 +247,9 @@ cudaError_t upload_step_tables(wdlb_ctx *ctx)
     std::vector<BatchItem> items;
     const int nb = (int)((ctx->N + 255) / 256);
     const int tx = (p.nx + 7) / 8, ty = (p.ny + 7) / 8, tz = (p.nz + 7) / 8;
-    auto bricks = [&]() {
-        for (int z = 0; z < tz; z++)
+    auto bricks = [&](int depth) {
+        const int bz = (p.nz + depth - 1) / depth;
+        for (int z = 0; z < bz; z++)
             for (int y = 0; y < ty; y++)
                 for (int x = 0; x < tx; x++) items.push_back(BatchItem{0, x, y, z});
     };
@@ -264,7 +267,7 @@ cudaError_t upload_step_tables(wdlb_ctx *ctx)
     LL.n_node_items = nb;
     if (p.ball_tiled) {
         LL.ball_items = dit + items.size();
-        bricks();
+        bricks(kBallTile);
         LL.n_ball_items = tx * ty * tz;
         LL.ball_smem = ball_tile_smem(p.ball_r, p.nball, ctx->opt.storage == WDLB_STORE_F64 ? 8 : 4);
     } else {
@@ -277,9 +280,10 @@ cudaError_t upload_step_tables(wdlb_ctx *ctx)
     G.walls = ctx->walls;
     G.tiled = p.tiled;
     G.closure = p.closure;
+    G.tile = p.tiled ? p.tile : -1;
     G.items = dit + items.size();
     if (p.tiled)
-        bricks();
+        bricks(tile_depth(p.tile));
     else
         blocks();
     G.nitems = (int)(items.size() - (G.items - dit));
@@ -367,6 +371,106 @@ wdlb_status stats(wdlb_ctx *ctx, int update_snap, double r[6])
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Tile autotuner: a process-wide table (storage, 2 sigma, walls, nz) -> tile
+// shape of the tiled shell kernel, filled on first use by timing every shape
+// on a scratch lattice of the key, or from the built-in table.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+    int storage, s2, walls, nz;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::make_tuple(storage, s2, walls, nz) < std::make_tuple(o.storage, o.s2, o.walls, o.nz);
+    }
+};
+
+std::mutex g_tune_mutex;
+std::map<TuneKey, int> g_tune;
+
+int two_sigma(double sigma)
+{
+    const double s2 = 2.0 * sigma;
+    return std::fabs(s2 - std::round(s2)) < 1e-12 ? (int)std::lround(s2) : 0;
+}
+
+// Whether the tiled shell kernel serves these arguments (the launchers apply
+// the same rule when preparing a context).
+bool tiled_applies(wdlb_lattice lat, double sigma, const wdlb_options &o)
+{
+    const int s2 = two_sigma(sigma);
+    return o.storage != WDLB_STORE_F64 && o.closure == WDLB_CLOSURE_CS && (s2 == 6 || s2 == 8 || s2 == 12) &&
+           lat.nx >= 8 && lat.ny >= 8;
+}
+
+// Built-in choice when no probe runs: the 512-thread shape for sigma 6 (one
+// 160 KB block per SM), else 8^3 bricks on 256 threads (two blocks per SM).
+int tile_builtin(int s2, int walls, int nz)
+{
+    (void)walls;
+    (void)nz;
+    return s2 == 12 ? WDLB_TILE_8x8x8_WIDE : WDLB_TILE_8x8x8;
+}
+
+// Time each shape's shell kernel on a scratch lattice of the key: nz as
+// given and a square cross-section of about 2^20 / nz nodes, so that the
+// kernel fills the GPU as a batch of pores does (a single small pore leaves
+// SMs idle and would favour shapes that merely make more blocks).  The
+// scratch contexts force their shape, so they do not come back here.
+wdlb_status probe_tiles(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_options &o, int *best,
+                        double ms[3])
+{
+    int side = (int)std::ceil(std::sqrt(double(1 << 20) / double(lat.nz)) / 8.0) * 8;
+    side = std::max(8, std::min(side, 512));
+    wdlb_lattice pl{side, side, lat.nz};
+    const long long N = (long long)pl.nx * pl.ny * pl.nz;
+    std::vector<double> n(N, 0.4 / (sigma * sigma * sigma));
+    if (walls)
+        for (long long i = 0; i < (long long)pl.nx * pl.ny; i++) n[i] = n[N - 1 - i] = 0.0;
+    const double g[3] = {1e-6, 0.0, 0.0};
+    *best = -1;
+    for (int v = 0; v < 3; v++) {
+        ms[v] = NAN;
+        wdlb_options po = o;
+        po.tile = v;
+        po.autotune = 0;
+        po.workspace = nullptr;
+        po.workspace_bytes = 0;
+        po.stream = nullptr;
+        po.n_ref = 0.0;
+        wdlb_ctx *c = nullptr;
+        if (wdlb_create(pl, sigma, walls, 1.0, g, &po, &c) != WDLB_OK) continue;
+        double t[3];
+        if (c->kp.tiled && c->kp.tile == v && wdlb_init_fields(c, n.data(), nullptr) == WDLB_OK &&
+            wdlb_profile_step(c, 2, t) == WDLB_OK && wdlb_profile_step(c, 6, t) == WDLB_OK)
+            ms[v] = t[2];
+        wdlb_destroy(c);
+        if (std::isfinite(ms[v]) && (*best < 0 || ms[v] < ms[*best])) *best = v;
+    }
+    return *best >= 0 ? WDLB_OK : WDLB_ERR_CUDA;
+}
+
+int choose_tile(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_options &o)
+{
+    if (!tiled_applies(lat, sigma, o)) return WDLB_TILE_8x8x8;
+    if (o.tile >= 0) return o.tile;
+    const TuneKey key{o.storage, two_sigma(sigma), walls, lat.nz};
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+    int v = tile_builtin(key.s2, walls, lat.nz);
+    if (o.autotune) {
+        int b = -1;
+        double ms[3];
+        if (probe_tiles(lat, sigma, walls, o, &b, ms) == WDLB_OK) v = b;
+    }
+    g_tune[key] = v;
+    return v;
+}
+
+}  // namespace
+
 extern "C" {
 
 void wdlb_default_options(wdlb_options *opt)
@@ -379,6 +483,8 @@ void wdlb_default_options(wdlb_options *opt)
     opt->interactions = 1;
     opt->k_cross = 2.0;
     opt->n_ref = 0.0;
+    opt->tile = WDLB_TILE_AUTO;
+    opt->autotune = 1;
 }
 
 wdlb_status wdlb_workspace_size(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_options *opt,
@@ -431,6 +537,7 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
     build_shell(sigma, ctx->tab.shell, &ctx->tab.wshell);
     ctx->L = &launchers_for(o.storage);
     set_params(ctx);
+    ctx->kp.tile = choose_tile(lat, sigma, walls, o);
     ctx->kp.tiled = ctx->L->prepare(ctx->kp) ? 1 : 0;
     set_reference(ctx, o.n_ref > 0 ? o.n_ref : 1.0);
     const int nshell = ctx->kp.nshell, nball = ctx->kp.nball;
@@ -641,7 +748,7 @@ wdlb_status wdlb_pore_average(wdlb_ctx *ctx, wdlb_pore_stats *out)
 
 // Steady-state residual: relative change per step of the pore flux sum(n u_x)
 // (FP64 reduction) between two tests `interval` steps apart.
-double flux_residual(wdlb_ctx *ctx, const double r[6], int64_t interval)
+static double flux_residual(wdlb_ctx *ctx, const double r[6], int64_t interval)
 {
     const double q = r[2];
     double res;
@@ -747,6 +854,41 @@ wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3])
     if (err != cudaSuccess) return cuda_fail(ctx, err, "profile step");
     for (int k = 0; k < 3; k++) ms[k] = acc[k] / double(nsteps);
     return check_status_word(ctx);
+}
+
+wdlb_status wdlb_autotune(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_options *opt, int32_t *best,
+                          double ms[3])
+{
+    wdlb_options o;
+    if (opt)
+        o = *opt;
+    else
+        wdlb_default_options(&o);
+    if (validate(lat, sigma, walls, &o) != WDLB_OK || !tiled_applies(lat, sigma, o)) return WDLB_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    int b = -1;
+    double t[3];
+    wdlb_status s = probe_tiles(lat, sigma, walls, o, &b, t);
+    if (s != WDLB_OK) return s;
+    g_tune[TuneKey{o.storage, two_sigma(sigma), walls, lat.nz}] = b;
+    if (best) *best = b;
+    if (ms)
+        for (int v = 0; v < 3; v++) ms[v] = t[v];
+    return WDLB_OK;
+}
+
+wdlb_status wdlb_tile_info(const wdlb_ctx *ctx, int32_t *tiled, int32_t *tile)
+{
+    if (!ctx) return WDLB_ERR_ARG;
+    if (tiled) *tiled = ctx->kp.tiled;
+    if (tile) *tile = ctx->kp.tiled ? ctx->kp.tile : -1;
+    return WDLB_OK;
+}
+
+void wdlb_autotune_reset(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune.clear();
 }
 
 int64_t wdlb_launch_count(const wdlb_ctx *ctx) { return ctx ? ctx->launches : 0; }
@@ -871,10 +1013,11 @@ wdlb_status batch_build(wdlb_batch *b)
     std::vector<BatchItem> node_items, ball_items, ball_node_items;
     size_t ball_smem = 0;
     struct Key {
-        int s2, walls, tiled, closure;
+        int s2, walls, tiled, closure, tile;
         bool operator<(const Key &o) const
         {
-            return std::make_tuple(s2, walls, tiled, closure) < std::make_tuple(o.s2, o.walls, o.tiled, o.closure);
+            return std::make_tuple(s2, walls, tiled, closure, tile) <
+                   std::make_tuple(o.s2, o.walls, o.tiled, o.closure, o.tile);
         }
     };
     std::map<Key, std::vector<BatchItem>> groups;
@@ -897,10 +1040,11 @@ wdlb_status batch_build(wdlb_batch *b)
         } else {
             for (int k = 0; k < (N + 255) / 256; k++) ball_node_items.push_back(BatchItem{s, k, 0, 0});
         }
-        Key key{c->kp.tiled ? c->kp.s2 : 0, c->walls, c->kp.tiled, c->kp.closure};
+        Key key{c->kp.tiled ? c->kp.s2 : 0, c->walls, c->kp.tiled, c->kp.closure, c->kp.tiled ? c->kp.tile : -1};
         auto &g = groups[key];
         if (c->kp.tiled) {
-            const int tx = (c->lat.nx + 7) / 8, ty = (c->lat.ny + 7) / 8, tz = (c->lat.nz + 7) / 8;
+            const int depth = tile_depth(c->kp.tile);
+            const int tx = (c->lat.nx + 7) / 8, ty = (c->lat.ny + 7) / 8, tz = (c->lat.nz + depth - 1) / depth;
             for (int z = 0; z < tz; z++)
                 for (int y = 0; y < ty; y++)
                     for (int x = 0; x < tx; x++) g.push_back(BatchItem{s, x, y, z});
@@ -941,6 +1085,7 @@ wdlb_status batch_build(wdlb_batch *b)
         G.walls = g.first.walls;
         G.tiled = g.first.tiled;
         G.closure = g.first.closure;
+        G.tile = g.first.tile;
         G.items = b->d_items + all.size();
         G.nitems = (int)g.second.size();
         all.insert(all.end(), g.second.begin(), g.second.end());

@@ -50,6 +50,7 @@ struct KParams {
     int closure, omega_mode, interactions;
     int s2;                  // 2 sigma if it is an integer, else 0 (selects a compiled shell)
     int tiled;               // 1: use the shared-memory tiled shell kernel
+    int tile;                // its shape (tile variant 0, 1, 2; see wdlb_shell_tiled.cuh)
     int ball_r;              // largest |component| of a ball vector (halo of the tiled ball sum)
     int ball_tiled;          // 1: use the shared-memory tiled ball sum
     double g[3];             // external acceleration
@@ -70,6 +71,9 @@ struct KParams {
 // Tiled ball sum: an 8 x 8 x 8 brick of nodes per block with a halo of
 // ball_r, the brick's n - n_off and the ball's offsets in shared memory.
 constexpr int kBallTile = 8;
+
+// Output brick depth of tile variant v of the tiled shell kernel.
+inline __host__ __device__ int tile_depth(int v) { return v == 2 ? 4 : 8; }
 constexpr size_t kBallTileMaxSmem = 48 * 1024;   // no opt-in attribute needed
 
 inline __host__ __device__ size_t ball_tile_smem(int ball_r, int nball, size_t tsize)

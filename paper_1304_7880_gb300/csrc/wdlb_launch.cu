@@ -64,14 +64,14 @@ __global__ void __launch_bounds__(256) k_step_shell(const KParams *P, const KBuf
 }
 
 #if WDLB_STORAGE != 0
-template <int S2, bool WALLS>
-__global__ void __launch_bounds__(tiled::threads_for(S2), tiled::blocks_per_sm(S2))
+template <int S2, int V, bool WALLS>
+__global__ void __launch_bounds__(tiled::threads_of(V), tiled::blocks_per_sm<S2, V>())
     k_step_shell_tiled(const KParams *P, const KBufs<S, float> *B, const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
     const KParams p = P[w.slot];
     const KBufs<S, float> b = B[w.slot];
-    tiled::tiled_body<S, S2, 0, WALLS, false>(p, b, w.bx, w.by, w.bz);
+    tiled::tiled_body<S, S2, V, 0, WALLS, false>(p, b, w.bx, w.by, w.bz);
 }
 #endif
 
@@ -100,13 +100,53 @@ void launch_fields_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st
 }
 
 #if WDLB_STORAGE != 0
-// The tiled kernel is compiled for the Carnahan-Starling closure (the default)
-// and sigma in {3, 4, 6}; other closures and sigmas use the generic kernel.
-template <int S2, bool WALLS>
+// The tiled kernel is compiled for the Carnahan-Starling closure (the default),
+// sigma in {3, 4, 6} and the three tile variants; other closures and sigmas
+// use the generic kernel.
+template <int S2, int V, bool WALLS>
 cudaError_t tiled_attr()
 {
-    return cudaFuncSetAttribute(k_step_shell_tiled<S2, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tiled::smem_bytes<S2>());
+    return cudaFuncSetAttribute(k_step_shell_tiled<S2, V, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tiled::smem_bytes<S2, V>());
+}
+
+template <int S2, int V>
+cudaError_t tiled_attr_w(bool walls)
+{
+    return walls ? tiled_attr<S2, V, true>() : tiled_attr<S2, V, false>();
+}
+
+template <int S2>
+cudaError_t tiled_attr_v(int v, bool walls)
+{
+    return v == 0 ? tiled_attr_w<S2, 0>(walls) : (v == 1 ? tiled_attr_w<S2, 1>(walls) : tiled_attr_w<S2, 2>(walls));
+}
+
+template <int S2, int V, bool WALLS>
+void launch_tiled_group(const BatchLaunch &L, const KBufs<S, float> *B, const BatchGroup &G, cudaStream_t st)
+{
+    k_step_shell_tiled<S2, V, WALLS>
+        <<<G.nitems, tiled::threads_of(V), tiled::smem_bytes<S2, V>(), st>>>(L.params, B, G.items);
+}
+
+template <int S2, int V>
+void launch_tiled_w(const BatchLaunch &L, const KBufs<S, float> *B, const BatchGroup &G, cudaStream_t st)
+{
+    if (G.walls)
+        launch_tiled_group<S2, V, true>(L, B, G, st);
+    else
+        launch_tiled_group<S2, V, false>(L, B, G, st);
+}
+
+template <int S2>
+void launch_tiled_v(const BatchLaunch &L, const KBufs<S, float> *B, const BatchGroup &G, cudaStream_t st)
+{
+    if (G.tile == 0)
+        launch_tiled_w<S2, 0>(L, B, G, st);
+    else if (G.tile == 1)
+        launch_tiled_w<S2, 1>(L, B, G, st);
+    else
+        launch_tiled_w<S2, 2>(L, B, G, st);
 }
 #endif
 
@@ -122,14 +162,11 @@ bool tiled_eligible(const KParams &p)
 
 bool do_prepare(const KParams &p)
 {
-    if (!tiled_eligible(p)) return false;
+    if (!tiled_eligible(p) || p.tile < 0 || p.tile >= tiled::kVariants) return false;
 #if WDLB_STORAGE != 0
-    cudaError_t e = cudaSuccess;
-    switch (p.s2) {
-    case 6: e = p.walls ? tiled_attr<6, true>() : tiled_attr<6, false>(); break;
-    case 8: e = p.walls ? tiled_attr<8, true>() : tiled_attr<8, false>(); break;
-    default: e = p.walls ? tiled_attr<12, true>() : tiled_attr<12, false>(); break;
-    }
+    const bool walls = p.walls != 0;
+    cudaError_t e = p.s2 == 6 ? tiled_attr_v<6>(p.tile, walls)
+                              : (p.s2 == 8 ? tiled_attr_v<8>(p.tile, walls) : tiled_attr_v<12>(p.tile, walls));
     return e == cudaSuccess;
 #else
     return false;
@@ -224,14 +261,12 @@ cudaError_t do_batch_step(const BatchLaunch &L, int parity, int part, cudaStream
         if (G.nitems == 0) continue;
 #if WDLB_STORAGE != 0
         if (G.tiled) {
-            const size_t sm = G.s2 == 6 ? tiled::smem_bytes<6>() : (G.s2 == 8 ? tiled::smem_bytes<8>()
-                                                                               : tiled::smem_bytes<12>());
-#define WDLB_TB(S2V, WV) \
-    k_step_shell_tiled<S2V, WV><<<G.nitems, tiled::threads_for(S2V), sm, st>>>(L.params, B, G.items)
-            if (G.s2 == 6) { if (G.walls) WDLB_TB(6, true); else WDLB_TB(6, false); }
-            else if (G.s2 == 8) { if (G.walls) WDLB_TB(8, true); else WDLB_TB(8, false); }
-            else { if (G.walls) WDLB_TB(12, true); else WDLB_TB(12, false); }
-#undef WDLB_TB
+            if (G.s2 == 6)
+                launch_tiled_v<6>(L, B, G, st);
+            else if (G.s2 == 8)
+                launch_tiled_v<8>(L, B, G, st);
+            else
+                launch_tiled_v<12>(L, B, G, st);
             *launches += 1;
             continue;
         }

@@ -40,7 +40,7 @@ struct BatchItem {
 
 // Shell launch of one group of slots with the same kernel variant.
 struct BatchGroup {
-    int s2, walls, tiled, closure;
+    int s2, walls, tiled, closure, tile;
     const BatchItem *items;
     int nitems;
 };
@@ -64,16 +64,6 @@ struct BatchLaunch {
 };
 
 constexpr size_t kKBufsMaxBytes = 256;   // room for one KBufs of any storage type in a table
-
-// Work items of one lattice stepped alone (a one-slot table): blocks of 256
-// nodes, 8^3 bricks, and the shell items (bricks when tiled, else blocks).
-inline int node_blocks(const KParams &p) { return (p.N + 255) / 256; }
-inline int brick_count(const KParams &p) { return ((p.nx + 7) / 8) * ((p.ny + 7) / 8) * ((p.nz + 7) / 8); }
-inline size_t single_items(const KParams &p)
-{
-    const int nb = node_blocks(p), nt = brick_count(p);
-    return size_t(nb) + 2 * size_t(nb > nt ? nb : nt);
-}
 
 struct Launchers {
     // per-context preparation outside any stream capture (kernel attributes);

@@ -1,12 +1,15 @@
-// Tiled shell kernel: the same step as k_shell_collide (steps 2 + 3 of
-// Sec. 5), in FP32, with the field tile and its shell halo staged in shared
-// memory.
+// Tiled shell kernel: the shell sums, collision and streaming of
+// shell_body (steps 2 + 3 of Sec. 5), in FP32, with the field tile and its
+// shell halo staged in shared memory.
 //
-// Block: an 8 x 8 x 8 brick of output nodes; 256 threads with two nodes each
-// (z and z + 4), two blocks per SM, where the staged tile is small enough
-// (sigma 3, 4); 512 threads with one node each, one block per SM, for
-// sigma 6, whose tile takes 160 KB of shared memory (16 warps per SM instead
-// of 8 hide more of the pair loop's latency).  Shared memory holds (8 + 2R)^3 nodes of (n - n_off, v_x, v_y,
+// Block: a brick of 8 x 8 x TZ output nodes.  Three shapes (tile variants),
+// chosen per (sigma, walls, nz) by the autotuner:
+//   0: TZ = 8, 256 threads, two nodes each (z and z + 4);
+//   1: TZ = 8, 512 threads, one node each (16 warps per SM when only one
+//      block fits, as for sigma 6, whose tile takes 160 KB);
+//   2: TZ = 4, 256 threads, one node each (less z padding in thin slits,
+//      more halo per node).
+// Shared memory holds (8 + 2R)^2 (TZ + 2R) nodes of (n - n_off, v_x, v_y,
 // v_z) and hb - h_off, R = floor(sigma + 1/2), with periodic wrap in x, y (and
 // z without walls) and n = 0 beyond the walls, so the shell loop needs no
 // bounds checks: a solid or missing neighbour has n = 0 and adds nothing.
@@ -14,7 +17,7 @@
 // (khat_x, khat_y, khat_z, offset of +e in the tile); the loop over them is
 // kept rolled (a few pairs per iteration) so the code stays in the
 // instruction cache.  Each pair goes through pair_weights and accumulate_pair,
-// the same arithmetic as k_shell_collide.
+// the same arithmetic as shell_body.
 #pragma once
 
 #include "wdlb_kernels.cuh"
@@ -22,10 +25,11 @@
 namespace wdlb {
 namespace tiled {
 
-constexpr int TX = 8, TY = 8, TZ = 8;
+constexpr int TX = 8, TY = 8;
+constexpr int kVariants = 3;
 
-constexpr int threads_for(int S2) { return S2 >= 12 ? 512 : 256; }
-constexpr int blocks_per_sm(int S2) { return S2 >= 12 ? 1 : 2; }
+constexpr int tz_of(int V) { return V == 2 ? 4 : 8; }
+constexpr int threads_of(int V) { return V == 1 ? 512 : 256; }
 
 constexpr int shell_radius(int S2) { return (S2 + 1) / 2; }
 
@@ -41,22 +45,31 @@ constexpr int shell_count(int S2)
     return m;
 }
 
-template <int S2>
+template <int S2, int V>
 constexpr size_t smem_bytes()
 {
     constexpr int R = shell_radius(S2);
-    constexpr size_t n = size_t(TX + 2 * R) * (TY + 2 * R) * (TZ + 2 * R);
+    constexpr size_t n = size_t(TX + 2 * R) * (TY + 2 * R) * (tz_of(V) + 2 * R);
     return n * (sizeof(float4) + sizeof(float)) + size_t(shell_count(S2) / 2) * sizeof(float4);
 }
 
-template <class S, int S2, int CL, bool WALLS, bool FIELDS>
+// Blocks per SM the launch bounds ask for: two where two blocks' shared
+// memory fits (227 KB per SM) and the threads are 256, else one.
+template <int S2, int V>
+constexpr int blocks_per_sm()
+{
+    return threads_of(V) == 256 && 2 * smem_bytes<S2, V>() <= 227 * 1024 ? 2 : 1;
+}
+
+template <class S, int S2, int V, int CL, bool WALLS, bool FIELDS>
 __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, float> &b, int bx, int by, int bz)
 {
     constexpr int R = shell_radius(S2);
+    constexpr int TZ = tz_of(V);
     constexpr int SX = TX + 2 * R, SY = TY + 2 * R, SZ = TZ + 2 * R;
     constexpr int NS = SX * SY * SZ;
     constexpr int NPAIR = shell_count(S2) / 2;
-    constexpr int NT = threads_for(S2);
+    constexpr int NT = threads_of(V);
     constexpr int ZSTEP = NT / (TX * TY);     // z rows covered by one pass of the block
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *sm4 = reinterpret_cast<float4 *>(smem_raw);

@@ -41,7 +41,7 @@ class wdlb_options(ctypes.Structure):
     _fields_ = [("closure", ctypes.c_int32), ("omega_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("interactions", ctypes.c_int32), ("k_cross", ctypes.c_double), ("n_ref", ctypes.c_double),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 
 class wdlb_pore_desc(ctypes.Structure):
@@ -88,6 +88,9 @@ def load_library(path: str = LIB_PATH):
         "wdlb_get_populations": (I32, [P, P]),
         "wdlb_pore_average": (I32, [P, P]),
         "wdlb_run_steady": (I32, [P, D, I32, I64, P, P]),
+        "wdlb_autotune": (I32, [wdlb_lattice, D, I32, P, P, P]),
+        "wdlb_tile_info": (I32, [P, P, P]),
+        "wdlb_autotune_reset": (None, []),
         "wdlb_velocity_set": (I32, [P, P]),
         "wdlb_stencil": (I32, [D, I32, P, I32, P, P]),
         "wdlb_profile_step": (I32, [P, I64, P]),
@@ -157,8 +160,9 @@ class Context:
 
 
 def wdlb_create(lattice, sigma, walls, tau, g=(0.0, 0.0, 0.0), closure="CS", omega_mode="const",
-                storage="f32", interactions=True, k_cross=2.0, n_ref=0.0, device=None):
-    """Create a context; device memory and stream come from PyTorch."""
+                storage="f32", interactions=True, k_cross=2.0, n_ref=0.0, device=None, tile=-1, autotune=True):
+    """Create a context; device memory and stream come from PyTorch.  tile: -1
+    (autotuner) or a forced tile shape 0, 1, 2 of the tiled shell kernel."""
     import torch
 
     lib = load_library()
@@ -172,6 +176,8 @@ def wdlb_create(lattice, sigma, walls, tau, g=(0.0, 0.0, 0.0), closure="CS", ome
     opt.interactions = 1 if interactions else 0
     opt.k_cross = float(k_cross)
     opt.n_ref = float(n_ref)
+    opt.tile = int(tile)
+    opt.autotune = 1 if autotune else 0
     walls_i = 1 if walls else 0
     nbytes = ctypes.c_uint64()
     _check(lib.wdlb_workspace_size(lat, float(sigma), walls_i, ctypes.byref(opt), ctypes.byref(nbytes)))
@@ -246,6 +252,38 @@ def wdlb_pore_average(ctx: Context) -> dict:
     st = wdlb_pore_stats()
     _check(lib.wdlb_pore_average(ctx.handle, ctypes.byref(st)), ctx)
     return {k: getattr(st, k) for k, _ in wdlb_pore_stats._fields_}
+
+
+def wdlb_autotune(lattice, sigma, walls, storage="f32", device=None):
+    """Time the tiled shell kernel's shapes for this (storage, sigma, walls, nz)
+    now and record the fastest; returns (best, [ms per step of shapes 0, 1, 2])."""
+    import torch
+
+    lib = load_library()
+    opt = wdlb_options()
+    lib.wdlb_default_options(ctypes.byref(opt))
+    opt.storage = STORAGES[storage]
+    nx, ny, nz = (int(v) for v in lattice)
+    best = ctypes.c_int32()
+    ms = (ctypes.c_double * 3)()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        st = lib.wdlb_autotune(wdlb_lattice(nx, ny, nz), float(sigma), 1 if walls else 0, ctypes.byref(opt),
+                               ctypes.byref(best), ms)
+    if st != WDLB_OK:
+        raise WDLBError(st, "wdlb_autotune")
+    return best.value, list(ms)
+
+
+def wdlb_tile_info(ctx: Context):
+    """(tiled, tile shape) of the shell kernel the context runs."""
+    tiled, tile = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().wdlb_tile_info(ctx.handle, ctypes.byref(tiled), ctypes.byref(tile)), ctx)
+    return bool(tiled.value), tile.value
+
+
+def wdlb_autotune_reset():
+    load_library().wdlb_autotune_reset()
 
 
 def wdlb_run_steady(ctx: Context, tol: float, check_every: int = 100, max_steps: int = 10 ** 7):

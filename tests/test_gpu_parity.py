@@ -149,6 +149,47 @@ def test_bulk_shear_wave_128_full_size(w, oracle_mod):
     assert abs(st1["mass"] - st0["mass"]) / st0["mass"] < 1e-6
 
 
+# FP32 shared-memory tiled kernel (sigma 3, 4, 6; Carnahan-Starling) on ragged
+# lattices: partial 8^3 bricks in every direction, halos that wrap more than
+# once (sigma 6 on 9 x 8 cross-sections), and walls.
+TILED_CASES = {
+    "s3_periodic_13x11x19": dict(nx=13, ny=11, nz=19, walls=False, sigma=3.0, tau=0.8, g=(0, 1e-5, 0)),
+    "s3_slit_9x12x22": dict(nx=9, ny=12, nz=22, walls=True, sigma=3.0, tau=1.0, g=(1e-5, 0, 0)),
+    "s4_periodic_17x9x12": dict(nx=17, ny=9, nz=12, walls=False, sigma=4.0, tau=1.0, g=(0, 0, 1e-5)),
+    "s4_slit_10x8x27": dict(nx=10, ny=8, nz=27, walls=True, sigma=4.0, tau=1.0, g=(1e-5, 0, 0)),
+    "s6_periodic_9x8x21": dict(nx=9, ny=8, nz=21, walls=False, sigma=6.0, tau=1.0, g=(1e-5, 0, 0)),
+    "s6_slit_12x9x35": dict(nx=12, ny=9, nz=35, walls=True, sigma=6.0, tau=1.0, g=(1e-5, 0, 0)),
+}
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("name", sorted(TILED_CASES))
+def test_tiled_fp32_ragged(w, oracle_mod, name, tile):
+    """20 steps from a noisy state (2 % density noise, 1e-3 velocities): the
+    FP32 tiled path, in each of its three tile shapes, within 1e-5 of the
+    oracle on n and u."""
+    p = TILED_CASES[name]
+    n, u = random_state((p["nz"], p["ny"], p["nx"]), p["sigma"], 0.4, 2e-2, 17, p["walls"])
+    ctx, o = make_pair(w, oracle_mod, p, n, u, "f32", tile=tile)
+    assert w.wdlb_tile_info(ctx) == (True, tile)
+    w.wdlb_step(ctx, 20)
+    o.step(20)
+    compare(ctx, o, p["walls"], "f32", w)
+
+
+def test_autotuner_records_and_applies_its_choice(w):
+    w.wdlb_autotune_reset()
+    best, ms = w.wdlb_autotune((16, 16, 41), 4.0, True)
+    assert best in (0, 1, 2) and all(np.isfinite(ms)) and ms[best] == min(ms)
+    ctx = w.wdlb_create((16, 16, 41), 4.0, True, 1.0, (1e-6, 0, 0), storage="f32")
+    assert w.wdlb_tile_info(ctx) == (True, best)
+    # keys the tiled kernel does not serve: per-node kernel
+    c64 = w.wdlb_create((16, 16, 41), 4.0, True, 1.0, (1e-6, 0, 0), storage="f64")
+    assert w.wdlb_tile_info(c64) == (False, -1)
+    with pytest.raises(w.WDLBError):
+        w.wdlb_autotune((16, 16, 41), 4.0, True, storage="f64")
+
+
 EDGE_CASES = {
     "column_slit": (dict(nx=1, ny=1, nz=40, walls=True, sigma=4.0, tau=1.0, g=(1e-5, 0, 0)), {}),
     "ragged_periodic_s3": (dict(nx=13, ny=7, nz=19, walls=False, sigma=3.0, tau=0.8, g=(0, 1e-5, 0)), {}),
