@@ -128,10 +128,13 @@ class ClockSampler:
 
 
 def kernel_source_hash():
+    """Hash of the files that define the step kernels' device code and of the
+    build flags (host-side launch code does not change a kernel's traffic)."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1304_7880_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+    pkg = os.path.join(ROOT, "paper_1304_7880_gb300")
+    for f in ("csrc/wdlb_common.cuh", "csrc/wdlb_kernels.cuh", "csrc/wdlb_shell_tiled.cuh",
+              "csrc/wdlb_step_kernels.cuh", "build.py"):
+        with open(os.path.join(pkg, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -229,7 +232,7 @@ SERVE_WORKLOAD = ("slit Poiseuille requests: sigma in {3,4,6}, H/sigma lognormal
                   "admission budget, FIFO admission, at most 48 pores stepped together")
 
 
-def run_single_pore(w, synth, np, count=4, tol=1e-8):
+def run_single_pore(w, synth, np, count=2, tol=1e-8):
     """The first `count` requests of the serving stream solved one at a time,
     alone on the GPU, on the plain FP64 path and on the FP32 path (same
     kernels as the batch), to the same steady-state tolerance; solves/s of
@@ -336,7 +339,7 @@ def run_ours(args):
     shape = (p["nx"], p["ny"], p["nz"])
 
     def make(storage):
-        ctx = w.wdlb_create(shape, p["sigma"], p["walls"], p["tau"], p["g"], storage=storage)
+        ctx = w.wdlb_create(shape, p["sigma"], p["walls"], p["tau"], p["g"], storage=storage, tile=args.tile)
         d_n = torch.from_numpy(n_h).cuda()
         d_u = torch.from_numpy(u_h).cuda()
         torch.cuda.synchronize()
@@ -346,6 +349,7 @@ def run_ours(args):
 
     # ---------------- device-resident timed region (FP32 path) ----------------
     ctx = make("f32")
+    tile_info = w.wdlb_tile_info(ctx)
     for _ in range(args.warmup):
         w.wdlb_profile_step(ctx, SUB)
         w.wdlb_pore_average(ctx)
@@ -376,7 +380,8 @@ def run_ours(args):
     if args.only_device:
         if rank == 0:
             print(json.dumps({"only_device": True, "value": value, "unit": UNIT, "ms_per_step": elapsed_ms / args.steps,
-                              "time_steps_per_step": SUB, "kernels_ms": kms, "gpu_launches": int(gpu_launches)}),
+                              "time_steps_per_step": SUB, "kernels_ms": kms, "gpu_launches": int(gpu_launches),
+                              "tile_shape": tile_info[1]}),
                   flush=True)
         if dist is not None:
             dist.destroy_process_group()
@@ -477,7 +482,8 @@ def run_ours(args):
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     step_ms = sum(kms)
     hbm_achieved = BYTES_PER_NODE["f32"] * N / (step_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "k_step_shell_tiled", "achieved": achieved_tflops, "peak": alu_peak,
+    kname = ("k_step_shell_tiled<float, 8, %d, false>" % tile_info[1]) if tile_info[0] else "k_step_shell<float, 0, false>"
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tflops, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak, "traffic": recorded_traffic(),
                 "peak_source": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts)",
                 "flops_per_node": flops_per_node,
@@ -496,7 +502,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "nodes": N, "time_steps_per_step": SUB,
                        "storage": "f32 deviation from w_q n_ref, FP64 reductions",
                        "l2": "no flush: populations 2 x 159 MB + fields exceed the 129 MB L2",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "shell_kernel": {"tiled": tile_info[0], "tile_shape": tile_info[1],
+                                        "chosen_by": "autotuner" if args.tile < 0 else "--tile"}},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hn.nbytes + hu.nbytes),
                     "d2h_bytes_per_step": int(on.nbytes + ou.nbytes),
@@ -522,6 +530,8 @@ def main():
     ap.add_argument("--only-device", action="store_true",
                     help="time only the device-resident loop (for profiling); no e2e, baseline or other paths")
     ap.add_argument("--sub", type=int, default=SUB, help="lattice time steps per benchmark step")
+    ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="tile shape of the tiled shell kernel (-1: autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

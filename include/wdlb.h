@@ -312,9 +312,11 @@ typedef struct {
     int64_t node_steps;       /* lattice-node updates executed so far */
 } wdlb_server_stats;
 
-/* opt as for wdlb_batch_create; hbm_budget: pool bytes for admitted pores;
- * max_active: slots; check_every: steps between residual tests.  Starts the
- * worker thread on the current device. */
+/* opt as for wdlb_batch_create, except that opt->autotune is taken as 0: the
+ * worker thread never runs a tile probe, its pores take the autotuner's table
+ * as it stands (call wdlb_autotune first to probe keys); hbm_budget: pool
+ * bytes for admitted pores; max_active: slots; check_every: steps between
+ * residual tests.  Starts the worker thread on the current device. */
 wdlb_status wdlb_server_create(const wdlb_options *opt, uint64_t hbm_budget, int32_t max_active,
                                int32_t check_every, wdlb_server **out);
 /* Queue a request (thread-safe, returns at once); *id identifies its result. */

@@ -332,7 +332,7 @@ wdlb_status init_from_stage(wdlb_ctx *ctx, const double *d_n, const double *d_u)
 wdlb_status step_direct(wdlb_ctx *ctx, int64_t n)
 {
     for (int64_t s = 0; s < n; s++) {
-        cudaError_t e = ctx->L->batch_step(ctx->launch, ctx->cur, -1, ctx->stream, &ctx->launches);
+        cudaError_t e = ctx->L->batch_step(ctx->launch, ctx->cur, -1, -1, ctx->stream, &ctx->launches);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernels");
         ctx->cur ^= 1;
     }
@@ -349,7 +349,7 @@ wdlb_status ensure_graph(wdlb_ctx *ctx)
     int cc = c;
     cudaError_t err = cudaSuccess;
     for (int s = 0; s < kGraphChunk && err == cudaSuccess; s++) {
-        err = ctx->L->batch_step(ctx->launch, cc, -1, ctx->stream, &dummy);
+        err = ctx->L->batch_step(ctx->launch, cc, -1, -1, ctx->stream, &dummy);
         cc ^= 1;
     }
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
@@ -697,7 +697,7 @@ wdlb_status wdlb_fields(wdlb_ctx *ctx, double *nbar, double *C, double *A, doubl
     char *save = reinterpret_cast<char *>(buf + 13 * N);
     cudaError_t e = cudaMemcpyAsync(save, ctx->dev.nu, nu_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
     for (int part = 0; part < 2 && e == cudaSuccess; part++)
-        e = ctx->L->batch_step(ctx->launch, ctx->cur, part, ctx->stream, &ctx->launches);
+        e = ctx->L->batch_step(ctx->launch, ctx->cur, part, -1, ctx->stream, &ctx->launches);
     if (e == cudaSuccess) e = ctx->L->fields(ctx->kp, ctx->dev, ctx->cur, dn, dC, dA, du, ctx->stream, &ctx->launches);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->dev.nu, save, nu_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e == cudaSuccess && nbar) e = cudaMemcpyAsync(nbar, dn, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
@@ -837,7 +837,7 @@ wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3])
         for (int part = 0; part < 3 && err == cudaSuccess; part++) {
             err = cudaEventRecord(ev[6 * s + 2 * part], ctx->stream);
             if (err == cudaSuccess)
-                err = ctx->L->batch_step(ctx->launch, ctx->cur, part, ctx->stream, &ctx->launches);
+                err = ctx->L->batch_step(ctx->launch, ctx->cur, part, -1, ctx->stream, &ctx->launches);
             if (err == cudaSuccess) err = cudaEventRecord(ev[6 * s + 2 * part + 1], ctx->stream);
         }
         ctx->cur ^= 1;
@@ -945,6 +945,8 @@ struct wdlb_batch {
     bool dirty = true;
     int64_t steps_since_build = 0;
     cudaGraphExec_t graph = nullptr;   // two steps: parity 0 then 1
+    cudaStream_t side[kMaxBatchGroups] = {};     // shell groups 1.. during capture
+    cudaEvent_t fork[kMaxBatchGroups] = {}, join[kMaxBatchGroups] = {};
     int64_t launches = 0;
     int64_t graph_launches = 0;        // kernels in one graph replay
     std::string err;
@@ -1110,22 +1112,61 @@ wdlb_status batch_build(wdlb_batch *b)
 wdlb_status batch_step_direct(wdlb_batch *b, int64_t n)
 {
     for (int64_t s = 0; s < n; s++) {
-        cudaError_t e = b->L->batch_step(b->launch, (int)(b->steps_since_build & 1), -1, b->stream, &b->launches);
+        cudaError_t e = b->L->batch_step(b->launch, (int)(b->steps_since_build & 1), -1, -1, b->stream, &b->launches);
         if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch step: %s", cudaGetErrorString(e));
         b->steps_since_build++;
     }
     return WDLB_OK;
 }
 
+// One time step inside the batch's graph capture.  The shell groups (pores of
+// different sigma, geometry or tile shape) touch disjoint pores, so with more
+// than one group their launches fork onto side streams after the smeared
+// density and join before the next step: the groups' last waves overlap
+// instead of leaving SMs idle between launches.
+cudaError_t batch_capture_step(wdlb_batch *b, int parity, int64_t *count)
+{
+    const BatchLaunch &L = b->launch;
+    cudaError_t e = b->L->batch_step(L, parity, 0, -1, b->stream, count);
+    if (e == cudaSuccess) e = b->L->batch_step(L, parity, 1, -1, b->stream, count);
+    if (e != cudaSuccess || L.ngroups <= 1) {
+        if (e == cudaSuccess) e = b->L->batch_step(L, parity, 2, -1, b->stream, count);
+        return e;
+    }
+    e = cudaEventRecord(b->fork[0], b->stream);
+    for (int g = 1; g < L.ngroups && e == cudaSuccess; g++) {
+        e = cudaStreamWaitEvent(b->side[g], b->fork[0], 0);
+        if (e == cudaSuccess) e = b->L->batch_step(L, parity, 2, g, b->side[g], count);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join[g], b->side[g]);
+    }
+    if (e == cudaSuccess) e = b->L->batch_step(L, parity, 2, 0, b->stream, count);
+    for (int g = 1; g < L.ngroups && e == cudaSuccess; g++) e = cudaStreamWaitEvent(b->stream, b->join[g], 0);
+    return e;
+}
+
+// Side streams and events of the fork/join (created outside any capture).
+cudaError_t batch_side_streams(wdlb_batch *b)
+{
+    cudaError_t e = cudaSuccess;
+    if (!b->fork[0]) e = cudaEventCreateWithFlags(&b->fork[0], cudaEventDisableTiming);
+    for (int g = 1; g < b->launch.ngroups && e == cudaSuccess; g++) {
+        if (!b->side[g]) e = cudaStreamCreateWithFlags(&b->side[g], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !b->join[g]) e = cudaEventCreateWithFlags(&b->join[g], cudaEventDisableTiming);
+    }
+    return e;
+}
+
 wdlb_status batch_ensure_graph(wdlb_batch *b)
 {
     if (b->graph) return WDLB_OK;
+    if (b->launch.ngroups > 1 && batch_side_streams(b) != cudaSuccess)
+        return bfail(b, WDLB_ERR_CUDA, "batch side streams");
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return bfail(b, WDLB_ERR_CUDA, "batch capture");
     int64_t count = 0;
-    cudaError_t e = b->L->batch_step(b->launch, 0, -1, b->stream, &count);
-    if (e == cudaSuccess) e = b->L->batch_step(b->launch, 1, -1, b->stream, &count);
+    cudaError_t e = cudaSuccess;
+    for (int parity = 0; parity < 2 && e == cudaSuccess; parity++) e = batch_capture_step(b, parity, &count);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -1355,6 +1396,11 @@ void wdlb_batch_destroy(wdlb_batch *b)
     for (auto &p : b->d_bufs)
         if (p) cudaFree(p);
     if (b->owns_pool && b->pool) cudaFree(b->pool);
+    for (int g = 0; g < kMaxBatchGroups; g++) {
+        if (b->side[g]) cudaStreamDestroy(b->side[g]);
+        if (b->fork[g]) cudaEventDestroy(b->fork[g]);
+        if (b->join[g]) cudaEventDestroy(b->join[g]);
+    }
     if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -1548,7 +1594,15 @@ wdlb_status wdlb_server_create(const wdlb_options *opt, uint64_t hbm_budget, int
     wdlb_server *s = new (std::nothrow) wdlb_server();
     if (!s) return WDLB_ERR_OOM;
     cudaGetDevice(&s->device);
-    wdlb_status st = wdlb_batch_create(opt, hbm_budget, max_active, &s->batch);
+    // no tile probes inside the worker thread: its pores take the autotuner's
+    // table as it stands (built-in rule for keys not yet in it)
+    wdlb_options o;
+    if (opt)
+        o = *opt;
+    else
+        wdlb_default_options(&o);
+    o.autotune = 0;
+    wdlb_status st = wdlb_batch_create(&o, hbm_budget, max_active, &s->batch);
     if (st != WDLB_OK) {
         delete s;
         return st;

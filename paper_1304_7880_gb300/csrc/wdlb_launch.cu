@@ -3,6 +3,7 @@
 #include "wdlb_kernels.cuh"
 #include "wdlb_launch.h"
 #include "wdlb_shell_tiled.cuh"
+#include "wdlb_step_kernels.cuh"
 
 #include <cstring>
 
@@ -25,55 +26,6 @@ typedef Store<S>::T T;
 constexpr int kThreads = 256;
 
 inline int blocks_for(int n) { return (n + kThreads - 1) / kThreads; }
-
-// ---- step kernels: one launch for all slots of a table ----
-// Every block copies its slot's parameters and buffer pointers into registers
-// and runs the per-block body.  A lattice stepped alone runs these kernels
-// through a one-slot table.
-__global__ void __launch_bounds__(256) k_step_moments(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
-{
-    const BatchItem w = it[blockIdx.x];
-    const KParams p = P[w.slot];
-    const KBufs<S, T> b = B[w.slot];
-    moments_body<S, false>(p, b, w.bx, nullptr, nullptr);
-}
-
-__global__ void __launch_bounds__(256) k_step_ball(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
-{
-    const BatchItem w = it[blockIdx.x];
-    const KParams p = P[w.slot];
-    const KBufs<S, T> b = B[w.slot];
-    ball_body<T>(p, b.nu, b.hb, b.ball, b.status, w.bx);
-}
-
-__global__ void __launch_bounds__(256) k_step_ball_tiled(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
-{
-    const BatchItem w = it[blockIdx.x];
-    const KParams p = P[w.slot];
-    const KBufs<S, T> b = B[w.slot];
-    ball_tiled_body<T>(p, b.nu, b.hb, b.ball, b.status, w.bx, w.by, w.bz);
-}
-
-template <int CL, bool WALLS>
-__global__ void __launch_bounds__(256) k_step_shell(const KParams *P, const KBufs<S, T> *B, const BatchItem *it)
-{
-    const BatchItem w = it[blockIdx.x];
-    const KParams p = P[w.slot];
-    const KBufs<S, T> b = B[w.slot];
-    shell_body<S, CL, WALLS, false>(p, b, w.bx);
-}
-
-#if WDLB_STORAGE != 0
-template <int S2, int V, bool WALLS>
-__global__ void __launch_bounds__(tiled::threads_of(V), tiled::blocks_per_sm<S2, V>())
-    k_step_shell_tiled(const KParams *P, const KBufs<S, float> *B, const BatchItem *it)
-{
-    const BatchItem w = it[blockIdx.x];
-    const KParams p = P[w.slot];
-    const KBufs<S, float> b = B[w.slot];
-    tiled::tiled_body<S, S2, V, 0, WALLS, false>(p, b, w.bx, w.by, w.bz);
-}
-#endif
 
 KBufs<S, T> typed(const DevBufs &d, int cur)
 {
@@ -106,7 +58,7 @@ void launch_fields_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st
 template <int S2, int V, bool WALLS>
 cudaError_t tiled_attr()
 {
-    return cudaFuncSetAttribute(k_step_shell_tiled<S2, V, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_step_shell_tiled<S, S2, V, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tiled::smem_bytes<S2, V>());
 }
 
@@ -125,7 +77,7 @@ cudaError_t tiled_attr_v(int v, bool walls)
 template <int S2, int V, bool WALLS>
 void launch_tiled_group(const BatchLaunch &L, const KBufs<S, float> *B, const BatchGroup &G, cudaStream_t st)
 {
-    k_step_shell_tiled<S2, V, WALLS>
+    k_step_shell_tiled<S, S2, V, WALLS>
         <<<G.nitems, tiled::threads_of(V), tiled::smem_bytes<S2, V>(), st>>>(L.params, B, G.items);
 }
 
@@ -238,27 +190,28 @@ void kbufs_fill(const DevBufs &d, int cur, void *out)
     std::memcpy(out, &b, sizeof(b));
 }
 
-cudaError_t do_batch_step(const BatchLaunch &L, int parity, int part, cudaStream_t st, int64_t *launches)
+cudaError_t do_batch_step(const BatchLaunch &L, int parity, int part, int group, cudaStream_t st,
+                          int64_t *launches)
 {
     const KBufs<S, T> *B = static_cast<const KBufs<S, T> *>(L.bufs[parity & 1]);
     if ((part < 0 || part == 0) && L.n_node_items > 0) {
-        k_step_moments<<<L.n_node_items, kThreads, 0, st>>>(L.params, B, L.node_items);
+        k_step_moments<S><<<L.n_node_items, kThreads, 0, st>>>(L.params, B, L.node_items);
         *launches += 1;
     }
     if (part < 0 || part == 1) {
         if (L.n_ball_items > 0) {
-            k_step_ball_tiled<<<L.n_ball_items, kThreads, L.ball_smem, st>>>(L.params, B, L.ball_items);
+            k_step_ball_tiled<S><<<L.n_ball_items, kThreads, L.ball_smem, st>>>(L.params, B, L.ball_items);
             *launches += 1;
         }
         if (L.n_ball_node_items > 0) {
-            k_step_ball<<<L.n_ball_node_items, kThreads, 0, st>>>(L.params, B, L.ball_node_items);
+            k_step_ball<S><<<L.n_ball_node_items, kThreads, 0, st>>>(L.params, B, L.ball_node_items);
             *launches += 1;
         }
     }
     if (part >= 0 && part != 2) return cudaGetLastError();
     for (int g = 0; g < L.ngroups; g++) {
         const BatchGroup &G = L.groups[g];
-        if (G.nitems == 0) continue;
+        if (G.nitems == 0 || (group >= 0 && g != group)) continue;
 #if WDLB_STORAGE != 0
         if (G.tiled) {
             if (G.s2 == 6)
@@ -271,7 +224,7 @@ cudaError_t do_batch_step(const BatchLaunch &L, int parity, int part, cudaStream
             continue;
         }
 #endif
-#define WDLB_SB(CLV, WV) k_step_shell<CLV, WV><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items)
+#define WDLB_SB(CLV, WV) k_step_shell<S, CLV, WV><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items)
         if (G.closure == 0) { if (G.walls) WDLB_SB(0, true); else WDLB_SB(0, false); }
         else if (G.closure == 1) { if (G.walls) WDLB_SB(1, true); else WDLB_SB(1, false); }
         else { if (G.walls) WDLB_SB(2, true); else WDLB_SB(2, false); }

@@ -74,10 +74,12 @@ struct Launchers {
     void (*kbufs_fill)(const DevBufs &, int cur, void *out);
     // one time step of every slot in the tables (input buffers of parity p);
     // part -1: all three kernels, 0: moments, 1: smeared density, 2: shell
-    // sums + collision + streaming.  A lattice stepped alone uses the same
-    // kernels through a one-slot table, so it steps bit-identically alone and
-    // in a batch.
-    cudaError_t (*batch_step)(const BatchLaunch &, int parity, int part, cudaStream_t, int64_t *launches);
+    // sums + collision + streaming (group -1: every shell group, else only
+    // L.groups[group]).  A lattice stepped alone uses the same kernels
+    // through a one-slot table, so it steps bit-identically alone and in a
+    // batch.
+    cudaError_t (*batch_step)(const BatchLaunch &, int parity, int part, int group, cudaStream_t,
+                              int64_t *launches);
     cudaError_t (*init)(const KParams &, const DevBufs &, int cur, const double *d_n, const double *d_u,
                         cudaStream_t, int64_t *launches);
     // shell fields of the state in buffer `cur` after its moments and smeared
