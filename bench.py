@@ -160,6 +160,35 @@ def recorded_traffic():
     return None
 
 
+class RankSync:
+    """Barrier and maximum over the ranks of a torchrun job (one replica per
+    GPU; no collective on the data path).  dist is torch.distributed with an
+    initialised process group, or None for one process; device is where the
+    reduction tensor lives (cuda for NCCL, cpu for gloo)."""
+
+    def __init__(self, dist, device):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x):
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def job_mlups(world, nodes, time_steps, seconds):
+    """Whole-job throughput of `world` replicas that each updated `nodes`
+    lattice nodes `time_steps` times in `seconds` (the slowest rank's time)."""
+    return world * nodes * time_steps / seconds / 1e6
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -317,16 +346,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    sync = RankSync(dist, "cuda")
+    barrier = sync.barrier
+    max_over_ranks = sync.max
 
     from paper_1304_7880_gb300 import build, synth
     if rank == 0:
@@ -375,7 +397,7 @@ def run_ours(args):
     clocks = sampler.stop() if rank == 0 else None
     gpu_launches = w.wdlb_launch_count(ctx) - launches0
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
-    value = world * N * SUB * args.steps / (elapsed_ms * 1e-3) / 1e6
+    value = job_mlups(world, N, SUB * args.steps, elapsed_ms * 1e-3)
     stats = w.wdlb_pore_average(ctx)
     if args.only_device:
         if rank == 0:
@@ -408,7 +430,7 @@ def run_ours(args):
         w.wdlb_moments(ctx, on, ou)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     barrier()
-    e2e_value = world * N * SUB * e2e_steps / e2e_s / 1e6
+    e2e_value = job_mlups(world, N, SUB * e2e_steps, e2e_s)
     assert np.isfinite(on).all()
 
     # ---------------- batched slit pores (one launch per phase for all pores) ----------------
@@ -434,7 +456,7 @@ def run_ours(args):
     bb.record(bt.stream)
     torch.cuda.synchronize()
     bt_ms = max_over_ranks(ba.elapsed_time(bb))
-    batched = {"value": world * nodes_b * SUB * breps / (bt_ms * 1e-3) / 1e6, "unit": UNIT, "pores": len(pores),
+    batched = {"value": job_mlups(world, nodes_b, SUB * breps, bt_ms * 1e-3), "unit": UNIT, "pores": len(pores),
                "nodes": nodes_b, "time_steps": SUB * breps, "gpu_launches": w.wdlb_batch_launch_count(bt) - bl0,
                "workload": "64 slit pores 32x32x(13..121), sigma=4, n* in [0.1, 0.6], g_x log-uniform "
                            "[1e-7, 1e-5], tau=1, FP32; one launch per phase for all pores, CUDA graph"}
@@ -462,7 +484,7 @@ def run_ours(args):
         b.record(c2.stream)
         torch.cuda.synchronize()
         t = max_over_ranks(a.elapsed_time(b))
-        mlups = world * N * sub * reps / (t * 1e-3) / 1e6
+        mlups = job_mlups(world, N, sub * reps, t * 1e-3)
         paths[storage] = {"value": mlups, "unit": UNIT, "kernels_ms": pk,
                           "hbm_frac_of_measured": mlups * 1e6 * BYTES_PER_NODE[storage] / 1e9
                           / measured_peaks()[0]["hbm_gbs"]}
