@@ -305,3 +305,68 @@ def test_step_before_init_is_rejected(w):
     with pytest.raises(w.WDLBError) as ei:
         w.wdlb_step(ctx, 1)
     assert ei.value.status == 6
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_uniform_rest_state_stays_at_rest(w, storage):
+    """A uniform density at rest is a fixed point of the scheme (every shell
+    sum cancels and the ball mean equals n); in deviation storage all stored
+    deviations are zero, so it stays so exactly."""
+    n0 = 0.45 / 64
+    ctx = w.wdlb_create((16, 12, 10), 4.0, False, 1.0, (0, 0, 0), storage=storage)
+    w.wdlb_init_fields(ctx, np.full((10, 12, 16), n0))
+    w.wdlb_step(ctx, 60)
+    n_g, u_g = w.wdlb_moments(ctx)
+    assert np.all(u_g == 0.0)
+    np.testing.assert_allclose(n_g, n0, rtol=1e-15 if storage == "f64" else 1e-7)
+
+
+def test_conservation_fp64_on_the_gpu(w):
+    """Mass in a slit and momentum in a periodic box at g = 0 are conserved to
+    round-off (pair antisymmetry of C; bounce-back walls)."""
+    n, u = random_state((21, 9, 10), 4.0, 0.4, 2e-2, 5, True)
+    ctx = w.wdlb_create((10, 9, 21), 4.0, True, 1.0, (0, 0, 0), storage="f64")
+    w.wdlb_init_fields(ctx, n, u)
+    m0 = w.wdlb_pore_average(ctx)["mass"]
+    w.wdlb_step(ctx, 300)
+    assert abs(w.wdlb_pore_average(ctx)["mass"] - m0) / m0 < 1e-13
+    n, u = random_state((12, 10, 11), 4.0, 0.4, 2e-2, 6, False)
+    ctx = w.wdlb_create((11, 10, 12), 4.0, False, 1.0, (0, 0, 0), storage="f64")
+    w.wdlb_init_fields(ctx, n, u)
+    f0 = w.wdlb_get_populations(ctx)
+    c, _ = w.wdlb_velocity_set()
+    p0 = c.astype(float).T @ f0.reshape(19, -1).sum(axis=1)
+    w.wdlb_step(ctx, 300)
+    f1 = w.wdlb_get_populations(ctx)
+    p1 = c.astype(float).T @ f1.reshape(19, -1).sum(axis=1)
+    assert np.max(np.abs(p1 - p0)) < 1e-12 * np.sum(f0)
+
+
+def test_zero_steps_and_one_fluid_layer(w, oracle_mod):
+    p = dict(nx=4, ny=3, nz=3, walls=True, sigma=1.0, tau=1.0, g=(1e-5, 0, 0))
+    n, u = random_state((3, 3, 4), 1.0, 0.3, 1e-2, 8, True)
+    ctx, o = make_pair(w, oracle_mod, p, n, u, "f64")
+    w.wdlb_step(ctx, 0)
+    compare(ctx, o, True, "f64", w)
+    w.wdlb_step(ctx, 25)
+    o.step(25)
+    compare(ctx, o, True, "f64", w)
+
+
+def test_largest_lattice_a_context_accepts(w):
+    """A context indexes nodes with int32 and 19 populations per node:
+    N < 2^31 / 32.  The largest such box (one node short) is created and
+    stepped; one node more is rejected."""
+    nmax = (1 << 31) // 32 - 1
+    nx = ny = 406
+    nz = nmax // (nx * ny)
+    ctx = w.wdlb_create((nx, ny, nz), 4.0, False, 1.0, (0, 0, 0), storage="f32")
+    n0 = 0.4 / 64
+    w.wdlb_init_fields(ctx, np.full((nz, ny, nx), n0))
+    w.wdlb_step(ctx, 2)
+    st = w.wdlb_pore_average(ctx)
+    assert st["mean_n"] == pytest.approx(n0, rel=1e-6)
+    w.wdlb_destroy(ctx)
+    del ctx
+    with pytest.raises(w.WDLBError):
+        w.wdlb_create((1, 1, (1 << 31) // 32), 4.0, False, 1.0, (0, 0, 0), storage="f32")

@@ -20,9 +20,10 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "slit_column_steady.txt")
 NZ, SIGMA, TAU, GX = 161, 4.0, 0.8, 1e-6
 # Both storages run three times the oracle's step count, which converges them
-# (the relative flux change per step falls below 1e-10 in FP32): comparing at a
-# 1e-8 or 1e-9 tolerance would measure unfinished convergence (the slowest
-# mode relaxes over ~1.7e4 steps) rather than precision.
+# down to their rounding noise (the FP32 pore flux then fluctuates by ~1e-9 to
+# 1e-8 per step): comparing at a 1e-8 or 1e-9 tolerance would measure
+# unfinished convergence (the slowest mode relaxes over ~1.7e4 steps) rather
+# than precision.
 STEP_FACTOR = 3
 # Per-quantity bounds against the oracle: (n relative, u_x / max|u_x|, flux
 # relative).  Measured (converged): FP32 n 1.4e-7 / 4.2e-7, u_x 1.0e-5 /
@@ -72,9 +73,6 @@ def test_steady_slit_against_oracle(w, storage, n_star):
     w.wdlb_init_fields(ctx, uniform_slit(8, n_star))
     steps = STEP_FACTOR * ref["steps"]
     w.wdlb_step(ctx, steps)
-    if storage == "f32":
-        _, res = w.wdlb_run_steady(ctx, 1e-9, 100, 100)    # one more check block: converged
-        assert res < 1e-9, res
     n_g, u_g = w.wdlb_moments(ctx)
     w.wdlb_destroy(ctx)
     # uniform in x and y
