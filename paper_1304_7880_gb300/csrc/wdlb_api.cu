@@ -404,13 +404,15 @@ bool tiled_applies(wdlb_lattice lat, double sigma, const wdlb_options &o)
            lat.nx >= 8 && lat.ny >= 8;
 }
 
-// Built-in choice when no probe runs: the 512-thread shape for sigma 6 (one
-// 160 KB block per SM), else 8^3 bricks on 256 threads (two blocks per SM).
+// Built-in choice when no probe runs (the winners of the probe at every nz
+// measured): the 512-thread shape for sigma 6 (one 160 KB block per SM),
+// 8 x 8 x 4 bricks for sigma 4 (three 61 KB blocks per SM), 8^3 bricks for
+// sigma 3 (three 55 KB blocks per SM).
 int tile_builtin(int s2, int walls, int nz)
 {
     (void)walls;
     (void)nz;
-    return s2 == 12 ? WDLB_TILE_8x8x8_WIDE : WDLB_TILE_8x8x8;
+    return s2 == 12 ? WDLB_TILE_8x8x8_WIDE : (s2 == 8 ? WDLB_TILE_8x8x4 : WDLB_TILE_8x8x8);
 }
 
 // Time each shape's shell kernel on a scratch lattice of the key: nz as

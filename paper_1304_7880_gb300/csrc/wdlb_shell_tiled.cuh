@@ -7,8 +7,8 @@
 //   0: TZ = 8, 256 threads, two nodes each (z and z + 4);
 //   1: TZ = 8, 512 threads, one node each (16 warps per SM when only one
 //      block fits, as for sigma 6, whose tile takes 160 KB);
-//   2: TZ = 4, 256 threads, one node each (less z padding in thin slits,
-//      more halo per node).
+//   2: TZ = 4, 256 threads, one node each (less z padding in thin slits and
+//      a smaller tile: three blocks per SM at sigma 4, more halo per node).
 // Shared memory holds (8 + 2R)^2 (TZ + 2R) nodes of (n - n_off, v_x, v_y,
 // v_z) and hb - h_off, R = floor(sigma + 1/2), with periodic wrap in x, y (and
 // z without walls) and n = 0 beyond the walls, so the shell loop needs no
@@ -53,12 +53,18 @@ constexpr size_t smem_bytes()
     return n * (sizeof(float4) + sizeof(float)) + size_t(shell_count(S2) / 2) * sizeof(float4);
 }
 
-// Blocks per SM the launch bounds ask for: two where two blocks' shared
-// memory fits (227 KB per SM) and the threads are 256, else one.
+// Blocks per SM the launch bounds ask for: for 256 threads, three where three
+// blocks' shared memory fits (227 KB per SM; the compiler then keeps to 85
+// registers per thread), else two where two fit, else one; one for 512
+// threads.  Three blocks measured 7-12 % faster than two for sigma 3 (8^3
+// bricks) and sigma 4 (8 x 8 x 4 bricks).
 template <int S2, int V>
 constexpr int blocks_per_sm()
 {
-    return threads_of(V) == 256 && 2 * smem_bytes<S2, V>() <= 227 * 1024 ? 2 : 1;
+    return threads_of(V) != 256                            ? 1
+           : 3 * smem_bytes<S2, V>() <= size_t(227) * 1024 ? 3
+           : 2 * smem_bytes<S2, V>() <= size_t(227) * 1024 ? 2
+                                                            : 1;
 }
 
 template <class S, int S2, int V, int CL, bool WALLS, bool FIELDS>

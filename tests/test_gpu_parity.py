@@ -177,6 +177,21 @@ def test_tiled_fp32_ragged(w, oracle_mod, name, tile):
     compare(ctx, o, p["walls"], "f32", w)
 
 
+@pytest.mark.parametrize("name", sorted(TILED_CASES))
+def test_tiled_fp16_ragged(w, oracle_mod, name):
+    """The FP16-storage tiled path (same kernel body, half-precision relative
+    deviations) on the ragged cases, in the autotuner's shape, within the FP16
+    bounds (bulk n 1e-6, u 5e-3; walls n 1e-3, u 0.2)."""
+    p = TILED_CASES[name]
+    n, u = random_state((p["nz"], p["ny"], p["nx"]), p["sigma"], 0.4, 2e-2, 17, p["walls"])
+    ctx, o = make_pair(w, oracle_mod, p, n, u, "f16")
+    assert w.wdlb_tile_info(ctx)[0]
+    w.wdlb_step(ctx, 20)
+    o.step(20)
+    tol = TOL_SLIT["f16"][:2] if p["walls"] else TOL["f16"]
+    compare(ctx, o, p["walls"], "f16", w, tol=tol)
+
+
 def test_autotuner_records_and_applies_its_choice(w):
     w.wdlb_autotune_reset()
     best, ms = w.wdlb_autotune((16, 16, 41), 4.0, True)
