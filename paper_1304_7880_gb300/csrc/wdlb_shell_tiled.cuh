@@ -96,13 +96,13 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
     for (int idx = threadIdx.x; idx < NS; idx += NT) {
         const int sx = idx % SX, sy = (idx / SX) % SY, sz = idx / (SX * SY);
         int gx = x0 - R + sx, gy = y0 - R + sy, gz = z0 - R + sz;
-        gx = ((gx % nx) + nx) % nx;
-        gy = ((gy % ny) + ny) % ny;
+        gx = wrap_coord(gx, nx);
+        gy = wrap_coord(gy, ny);
         bool inside = true;
         if (WALLS)
             inside = gz >= 0 && gz < nz;
         else
-            gz = ((gz % nz) + nz) % nz;
+            gz = wrap_coord(gz, nz);
         float4 v = make_float4(-noff, 0.f, 0.f, 0.f);   // beyond a wall: n = 0
         float h = -hoff;
         if (inside) {
