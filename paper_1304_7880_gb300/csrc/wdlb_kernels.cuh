@@ -236,6 +236,57 @@ __device__ __forceinline__ void ball_tiled_body(const KParams &p, const V4<T> *n
     }
 }
 
+// ball_tiled_body with 2 sigma = S2 known at compile time (sigma 3, 4, 6): the
+// brick side and the ball's offsets are constants, and the points are added
+// in the order of the host's ball table (dx, then dy, then dz ascending), so
+// the sums are bitwise those of ball_body and ball_tiled_body.
+template <class T, int S2>
+__device__ __forceinline__ void ball_brick_ct(const KParams &p, const V4<T> *nu, T *hb, int *status, int bx,
+                                              int by, int bz)
+{
+    constexpr int R = S2 / 4;                       // floor(sigma / 2)
+    constexpr int SX = kBallTile + 2 * R, NS = SX * SX * SX;
+    extern __shared__ __align__(16) unsigned char ball_smem[];
+    T *sn = reinterpret_cast<T *>(ball_smem);
+    const T noff = T(p.n_off);
+    const int x0 = bx * kBallTile, y0 = by * kBallTile, z0 = bz * kBallTile;
+    for (int idx = threadIdx.x; idx < NS; idx += blockDim.x) {
+        const int sx = idx % SX, sy = (idx / SX) % SX, sz = idx / (SX * SX);
+        const int gx = wrap_coord(x0 - R + sx, p.nx), gy = wrap_coord(y0 - R + sy, p.ny);
+        int gz = z0 - R + sz;
+        bool inside = true;
+        if (p.walls)
+            inside = gz >= 0 && gz < p.nz;
+        else
+            gz = wrap_coord(gz, p.nz);
+        sn[idx] = inside ? nu[gx + p.nx * (gy + p.ny * gz)].x : -noff;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tzb = threadIdx.x >> 6;
+    for (int half = 0; half < 2; half++) {
+        const int tz = tzb + 4 * half;
+        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+        if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
+        const int i = x + p.nx * (y + p.ny * z);
+        if (solid_plane(p, z)) {
+            hb[i] = -T(p.h_off);
+            continue;
+        }
+        const T *c = sn + (tx + R) + SX * ((ty + R) + SX * (tz + R));
+        T sum = T(0);
+#pragma unroll
+        for (int dx = -R; dx <= R; dx++)
+#pragma unroll
+            for (int dy = -R; dy <= R; dy++)
+#pragma unroll
+                for (int dz = -R; dz <= R; dz++)
+                    if (16 * (dx * dx + dy * dy + dz * dz) <= S2 * S2) sum += c[dx + SX * (dy + SX * dz)];
+        T dh = T(p.c_half) * sum;
+        if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
+        hb[i] = dh;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Pair weights of a (+e, -e) pair of the contact shell.  With
 // q = g2(chi_mid) n(r+e) (without the quadrature weight), chi_mid/2 =

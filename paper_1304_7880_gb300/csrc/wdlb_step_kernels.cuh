@@ -39,7 +39,13 @@ __global__ void __launch_bounds__(256) k_step_ball_tiled(const KParams *P, const
     const BatchItem w = it[blockIdx.x];
     const KParams p = P[w.slot];
     const KBufs<S, typename Store<S>::T> b = B[w.slot];
-    ball_tiled_body<typename Store<S>::T>(p, b.nu, b.hb, b.ball, b.status, w.bx, w.by, w.bz);
+    typedef typename Store<S>::T T;
+    switch (p.s2) {      // uniform over the block (one slot per block)
+    case 6: ball_brick_ct<T, 6>(p, b.nu, b.hb, b.status, w.bx, w.by, w.bz); break;
+    case 8: ball_brick_ct<T, 8>(p, b.nu, b.hb, b.status, w.bx, w.by, w.bz); break;
+    case 12: ball_brick_ct<T, 12>(p, b.nu, b.hb, b.status, w.bx, w.by, w.bz); break;
+    default: ball_tiled_body<T>(p, b.nu, b.hb, b.ball, b.status, w.bx, w.by, w.bz); break;
+    }
 }
 
 template <class S, int CL, bool WALLS>
