@@ -385,3 +385,51 @@ def test_largest_lattice_a_context_accepts(w):
     del ctx
     with pytest.raises(w.WDLBError):
         w.wdlb_create((1, 1, (1 << 31) // 32), 4.0, False, 1.0, (0, 0, 0), storage="f32")
+
+
+def test_bulk_128_shear_wave_decay_over_5000_steps(w, oracle_mod):
+    """The 128^3 bulk configuration (FP32, seeded density noise) run for 5000
+    steps: the decay rate of its shear wave (the viscosity it measures) equals
+    the oracle's on the exact 1 x 1 x 128 column of the same wave (1e-3) and
+    the discrete closed form of kinetic, cross-over and collisional parts
+    (1 %)."""
+    import math
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_physics import shear_theory
+    L, steps, every = 128, 5000, 500
+    q = 2 * math.pi / L
+    z = np.arange(L)
+    sz = np.sin(q * z)
+
+    def amplitude(u):
+        return 2.0 / L * float(np.sum(u[0].mean(axis=(1, 2)) * sz))
+
+    p, n, u = synth.bulk_shear_128()
+    ctx = w.wdlb_create((L, L, L), p["sigma"], False, p["tau"], p["g"], storage="f32")
+    w.wdlb_init_fields(ctx, n, u)
+    t, a = [], []
+    for k in range(steps // every):
+        w.wdlb_step(ctx, every)
+        if (k + 1) * every >= 1000:
+            t.append((k + 1) * every)
+            a.append(amplitude(w.wdlb_moments(ctx)[1]))
+    w.wdlb_destroy(ctx)
+    rate_gpu = -np.polyfit(t, np.log(a), 1)[0]
+    # oracle: the same wave on the column (no density noise: x-y uniform)
+    n0 = n.mean()
+    o = oracle_mod.Oracle(1, 1, L, False, p["sigma"], p["tau"])
+    uc = np.zeros((3, L, 1, 1))
+    uc[0, :, 0, 0] = 1e-4 * sz
+    o.init(np.full((L, 1, 1), n0), uc)
+    to, ao = [], []
+    for k in range(steps // every):
+        o.step(every)
+        if (k + 1) * every >= 1000:
+            to.append((k + 1) * every)
+            ao.append(2.0 / L * float(np.sum(o.moments()[1][0, :, 0, 0] * sz)))
+    rate_oracle = -np.polyfit(to, np.log(ao), 1)[0]
+    kin, cross, coll = shear_theory(L, p["sigma"], n0 * p["sigma"] ** 3, p["tau"], 2.0)
+    assert rate_gpu == pytest.approx(rate_oracle, rel=1e-3)
+    assert rate_gpu == pytest.approx(kin + cross + coll, rel=1e-2)

@@ -71,3 +71,28 @@ def test_uniform_rest_state_is_stationary(oracle_mod):
     f0 = o.populations()
     o.step(20)
     np.testing.assert_allclose(o.populations(), f0, rtol=1e-13)
+
+
+def test_column_equals_uniform_slab(oracle_mod):
+    """A state uniform in x and y is the same on a 1 x 1 x nz column (every
+    shell and ball vector wraps onto it) as on a wider slab; the steady slit
+    fixtures rely on it."""
+    nz, sigma = 21, 4.0
+    z = np.arange(nz)
+    prof = (0.45 / 64) * (1.0 + 0.05 * np.sin(2 * np.pi * z / (nz - 2)))
+    prof[0] = prof[-1] = 0.0
+    ux = 1e-4 * np.sin(np.pi * z / (nz - 1))
+    ux[0] = ux[-1] = 0.0
+    out = []
+    for nxy in (1, 5):
+        n = np.broadcast_to(prof[:, None, None], (nz, nxy, nxy)).copy()
+        u = np.zeros((3, nz, nxy, nxy))
+        u[0] = ux[:, None, None]
+        o = oracle_mod.Oracle(nxy, nxy, nz, True, sigma, 0.9, (1e-6, 0, 0))
+        o.init(n, u)
+        o.step(30)
+        nn, uu = o.moments()
+        out.append((nn[:, 0, 0], uu[:, :, 0, 0]))
+        assert np.abs(nn - nn[:, :1, :1]).max() == 0.0 and np.abs(uu - uu[:, :, :1, :1]).max() == 0.0
+    np.testing.assert_allclose(out[0][0], out[1][0], rtol=1e-14)
+    np.testing.assert_allclose(out[0][1], out[1][1], rtol=0, atol=1e-14 * np.abs(out[1][1]).max())
