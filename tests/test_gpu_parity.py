@@ -389,32 +389,35 @@ def test_largest_lattice_a_context_accepts(w):
 
 def test_bulk_128_shear_wave_decay_over_5000_steps(w, oracle_mod):
     """The 128^3 bulk configuration (FP32, seeded density noise) run for 5000
-    steps: the decay rate of its shear wave (the viscosity it measures) equals
-    the oracle's on the exact 1 x 1 x 128 column of the same wave (1e-3) and
-    the discrete closed form of kinetic, cross-over and collisional parts
-    (1 %)."""
+    steps.  The decay rate of its shear wave (the viscosity it measures),
+    fitted over steps 500-2500 while the amplitude (1e-5 .. 3e-10) is far
+    above round-off, equals the oracle's on the exact 1 x 1 x 128 column of
+    the same wave (1e-4; measured 4e-6) and the discrete closed form of
+    kinetic, cross-over and collisional parts (1 %).  By step 5000 the wave
+    has decayed by more than eight orders and stays decayed."""
     import math
     import sys
     import os
     sys.path.insert(0, os.path.dirname(__file__))
     from test_oracle_physics import shear_theory
-    L, steps, every = 128, 5000, 500
+    L, steps, every, fit_lo, fit_hi = 128, 5000, 250, 500, 2500
     q = 2 * math.pi / L
     z = np.arange(L)
     sz = np.sin(q * z)
 
-    def amplitude(u):
-        return 2.0 / L * float(np.sum(u[0].mean(axis=(1, 2)) * sz))
+    def amplitude(ux):
+        return 2.0 / L * float(np.sum(ux * sz))
 
     p, n, u = synth.bulk_shear_128()
     ctx = w.wdlb_create((L, L, L), p["sigma"], False, p["tau"], p["g"], storage="f32")
     w.wdlb_init_fields(ctx, n, u)
     t, a = [], []
-    for k in range(steps // every):
+    for k in range(1, steps // every + 1):
         w.wdlb_step(ctx, every)
-        if (k + 1) * every >= 1000:
-            t.append((k + 1) * every)
-            a.append(amplitude(w.wdlb_moments(ctx)[1]))
+        if fit_lo <= k * every <= fit_hi:
+            t.append(k * every)
+            a.append(amplitude(w.wdlb_moments(ctx)[1][0].mean(axis=(1, 2))))
+    a_end = amplitude(w.wdlb_moments(ctx)[1][0].mean(axis=(1, 2)))
     w.wdlb_destroy(ctx)
     rate_gpu = -np.polyfit(t, np.log(a), 1)[0]
     # oracle: the same wave on the column (no density noise: x-y uniform)
@@ -423,13 +426,37 @@ def test_bulk_128_shear_wave_decay_over_5000_steps(w, oracle_mod):
     uc = np.zeros((3, L, 1, 1))
     uc[0, :, 0, 0] = 1e-4 * sz
     o.init(np.full((L, 1, 1), n0), uc)
-    to, ao = [], []
-    for k in range(steps // every):
+    ao = []
+    for k in range(1, fit_hi // every + 1):
         o.step(every)
-        if (k + 1) * every >= 1000:
-            to.append((k + 1) * every)
-            ao.append(2.0 / L * float(np.sum(o.moments()[1][0, :, 0, 0] * sz)))
-    rate_oracle = -np.polyfit(to, np.log(ao), 1)[0]
+        if k * every >= fit_lo:
+            ao.append(amplitude(o.moments()[1][0, :, 0, 0]))
+    rate_oracle = -np.polyfit(t, np.log(ao), 1)[0]
     kin, cross, coll = shear_theory(L, p["sigma"], n0 * p["sigma"] ** 3, p["tau"], 2.0)
-    assert rate_gpu == pytest.approx(rate_oracle, rel=1e-3)
+    assert rate_gpu == pytest.approx(rate_oracle, rel=1e-4)
     assert rate_gpu == pytest.approx(kin + cross + coll, rel=1e-2)
+    assert abs(a_end) < 1e-12
+
+
+def test_checkpoint_resumes_bit_for_bit(w):
+    """Save after 70 steps; 40 more steps from the saved state, in the same
+    context and in a fresh one, give the populations of an uninterrupted run;
+    a state of another lattice is refused."""
+    p, n, u = synth.slit_poiseuille(16, 16, 25, 0.4, 4.0, 1.0, 1e-6, seed=12)
+    ctx = w.wdlb_create((16, 16, 25), 4.0, True, 1.0, p["g"], storage="f32")
+    w.wdlb_init_fields(ctx, n, u)
+    w.wdlb_step(ctx, 70)
+    state = w.wdlb_save_state(ctx)
+    w.wdlb_step(ctx, 40)
+    f_ref = w.wdlb_get_populations(ctx)
+    w.wdlb_load_state(ctx, state)
+    w.wdlb_step(ctx, 40)
+    assert np.array_equal(w.wdlb_get_populations(ctx), f_ref)
+    assert w.wdlb_pore_average(ctx)["steps"] == 110
+    fresh = w.wdlb_create((16, 16, 25), 4.0, True, 1.0, p["g"], storage="f32")
+    w.wdlb_load_state(fresh, state)
+    w.wdlb_step(fresh, 40)
+    assert np.array_equal(w.wdlb_get_populations(fresh), f_ref)
+    other = w.wdlb_create((16, 16, 27), 4.0, True, 1.0, p["g"], storage="f32")
+    with pytest.raises(w.WDLBError):
+        w.wdlb_load_state(other, state)
