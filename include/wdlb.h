@@ -156,6 +156,18 @@ wdlb_status wdlb_fields(wdlb_ctx *ctx, double *nbar, double *C, double *A, doubl
  * order of wdlb_velocity_set), solid nodes 0.  Synchronous. */
 wdlb_status wdlb_get_populations(wdlb_ctx *ctx, double *f);
 
+/* Checkpoint and resume (no counterpart in the paper).  The state of an
+ * initialised context is its populations as stored, the per-node storage
+ * scale, the field velocity of the last moments pass (the predictor's v_prev,
+ * with n - n_off), C_prev, t_prev, the reference density and the step count;
+ * restoring it continues the run bit for bit.  The buffer is an opaque host
+ * blob of wdlb_state_bytes bytes, caller-owned, valid for a context with the
+ * same lattice, walls, sigma, tau and storage (WDLB_ERR_ARG otherwise, and
+ * for a buffer that is too small or not a saved state).  Synchronous. */
+wdlb_status wdlb_state_bytes(const wdlb_ctx *ctx, uint64_t *bytes);
+wdlb_status wdlb_save_state(wdlb_ctx *ctx, void *host, uint64_t bytes);
+wdlb_status wdlb_load_state(wdlb_ctx *ctx, const void *host, uint64_t bytes);
+
 /* Pore-averaged quantities (abstract: pore-averaged properties), reduced in
  * FP64 on the device over fluid nodes: mean density, mean u_x, flux
  * sum(n u_x)/(nx ny), mass sum(n), eta_eff = <n> g_x H^2 / (12 <u_x>) with

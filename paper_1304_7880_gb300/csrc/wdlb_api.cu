@@ -858,6 +858,91 @@ wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3])
     return check_status_word(ctx);
 }
 
+// ---- checkpoint ------------------------------------------------------------
+namespace {
+
+struct StateHeader {
+    uint64_t magic;
+    int32_t version, storage, nx, ny, nz, walls;
+    int64_t N, steps;
+    double sigma, tau, n_ref;
+};
+constexpr uint64_t kStateMagic = 0x3137454b50444c57ull;   // "WLDPKE71"
+
+// Device regions of the state, in blob order: (offset in the context's
+// memory, bytes).
+std::vector<std::pair<size_t, size_t>> state_regions(const wdlb_ctx *ctx)
+{
+    const Layout &L = ctx->lay;
+    const size_t sS = storage_bytes(ctx->opt.storage), sT = compute_bytes(ctx->opt.storage);
+    const size_t P = (size_t)ctx->Npad;
+    return {{L.f[ctx->cur], NQ * P * sS}, {L.nu, 4 * P * sT}, {L.cprev, 3 * P * sT}, {L.tprev, P * sT},
+            {L.nscale, P * sT}};
+}
+
+}  // namespace
+
+wdlb_status wdlb_state_bytes(const wdlb_ctx *ctx, uint64_t *bytes)
+{
+    if (!ctx || !bytes) return WDLB_ERR_ARG;
+    uint64_t b = sizeof(StateHeader);
+    for (auto &r : state_regions(ctx)) b += r.second;
+    *bytes = b;
+    return WDLB_OK;
+}
+
+wdlb_status wdlb_save_state(wdlb_ctx *ctx, void *host, uint64_t bytes)
+{
+    if (!ctx || !host) return ctx ? fail(ctx, WDLB_ERR_ARG, "host is NULL") : WDLB_ERR_ARG;
+    if (!ctx->initialised) return fail(ctx, WDLB_ERR_STATE, "save before init");
+    uint64_t need = 0;
+    wdlb_state_bytes(ctx, &need);
+    if (bytes < need) return fail(ctx, WDLB_ERR_ARG, "state buffer too small (%llu < %llu)",
+                                  (unsigned long long)bytes, (unsigned long long)need);
+    StateHeader h{kStateMagic, 1, ctx->opt.storage, ctx->lat.nx, ctx->lat.ny, ctx->lat.nz, ctx->walls,
+                  ctx->N, ctx->steps, ctx->sigma, ctx->tau, ctx->kp.n_off};
+    char *out = static_cast<char *>(host);
+    std::memcpy(out, &h, sizeof(h));
+    size_t off = sizeof(h);
+    for (auto &r : state_regions(ctx)) {
+        WDLB_CUDA(ctx, cudaMemcpyAsync(out + off, ctx->base + r.first, r.second, cudaMemcpyDeviceToHost, ctx->stream));
+        off += r.second;
+    }
+    WDLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return WDLB_OK;
+}
+
+wdlb_status wdlb_load_state(wdlb_ctx *ctx, const void *host, uint64_t bytes)
+{
+    if (!ctx || !host) return ctx ? fail(ctx, WDLB_ERR_ARG, "host is NULL") : WDLB_ERR_ARG;
+    uint64_t need = 0;
+    wdlb_state_bytes(ctx, &need);
+    if (bytes < need) return fail(ctx, WDLB_ERR_ARG, "state buffer too small");
+    StateHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    if (h.magic != kStateMagic || h.version != 1) return fail(ctx, WDLB_ERR_ARG, "not a saved state");
+    if (h.storage != ctx->opt.storage || h.nx != ctx->lat.nx || h.ny != ctx->lat.ny || h.nz != ctx->lat.nz ||
+        h.walls != ctx->walls || h.N != ctx->N || h.sigma != ctx->sigma || h.tau != ctx->tau)
+        return fail(ctx, WDLB_ERR_ARG, "saved state belongs to another lattice or configuration");
+    set_reference(ctx, h.n_ref);
+    drop_graphs(ctx);
+    WDLB_CUDA(ctx, cudaMemcpyAsync(const_cast<KParams *>(ctx->launch.params), &ctx->kp, sizeof(KParams),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+    const char *in = static_cast<const char *>(host);
+    size_t off = sizeof(h);
+    for (auto &r : state_regions(ctx)) {
+        WDLB_CUDA(ctx, cudaMemcpyAsync(ctx->base + r.first, in + off, r.second, cudaMemcpyHostToDevice, ctx->stream));
+        off += r.second;
+    }
+    WDLB_CUDA(ctx, cudaMemsetAsync(ctx->dev.status, 0, sizeof(int), ctx->stream));
+    WDLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->initialised = true;
+    ctx->steps = h.steps;
+    ctx->last_residual = NAN;
+    ctx->prev_flux = NAN;
+    return WDLB_OK;
+}
+
 wdlb_status wdlb_autotune(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_options *opt, int32_t *best,
                           double ms[3])
 {

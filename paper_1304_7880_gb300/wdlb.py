@@ -89,6 +89,9 @@ def load_library(path: str = LIB_PATH):
         "wdlb_pore_average": (I32, [P, P]),
         "wdlb_run_steady": (I32, [P, D, I32, I64, P, P]),
         "wdlb_autotune": (I32, [wdlb_lattice, D, I32, P, P, P]),
+        "wdlb_state_bytes": (I32, [P, P]),
+        "wdlb_save_state": (I32, [P, P, ctypes.c_uint64]),
+        "wdlb_load_state": (I32, [P, P, ctypes.c_uint64]),
         "wdlb_tile_info": (I32, [P, P, P]),
         "wdlb_autotune_reset": (None, []),
         "wdlb_velocity_set": (I32, [P, P]),
@@ -252,6 +255,22 @@ def wdlb_pore_average(ctx: Context) -> dict:
     st = wdlb_pore_stats()
     _check(lib.wdlb_pore_average(ctx.handle, ctypes.byref(st)), ctx)
     return {k: getattr(st, k) for k, _ in wdlb_pore_stats._fields_}
+
+
+def wdlb_save_state(ctx: Context) -> np.ndarray:
+    """Checkpoint of the context's state (an opaque byte array)."""
+    lib = load_library()
+    nb = ctypes.c_uint64()
+    _check(lib.wdlb_state_bytes(ctx.handle, ctypes.byref(nb)), ctx)
+    buf = np.zeros(int(nb.value), dtype=np.uint8)
+    _check(lib.wdlb_save_state(ctx.handle, _ptr(buf), ctypes.c_uint64(buf.nbytes)), ctx)
+    return buf
+
+
+def wdlb_load_state(ctx: Context, buf: np.ndarray):
+    """Restore a checkpoint taken from a context of the same configuration."""
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(load_library().wdlb_load_state(ctx.handle, _ptr(buf), ctypes.c_uint64(buf.nbytes)), ctx)
 
 
 def wdlb_autotune(lattice, sigma, walls, storage="f32", device=None):

@@ -136,3 +136,28 @@ def test_batch_residuals_and_status(w):
     assert res[s] < 1e-7 and st[s] == 0
     assert np.isnan(res[(s + 1) % 4]) and st[(s + 1) % 4] == -1
     w.wdlb_batch_destroy(b)
+
+
+def test_a_failing_pore_is_flagged_alone(w):
+    """Per-pore failure detection.  A NaN in a pore's initial density (made on
+    the host) is refused at admission; a pore whose state turns non-physical
+    while stepping (smeared packing fraction >= 1) marks only its own slot
+    unstable, and the other pore steps on exactly as it does alone."""
+    b = w.wdlb_batch_create(4, 64 << 20, storage="f32")
+    lat, sigma, walls, tau, g, nstar, seed = PORES[0]
+    n, u = pore_fields(lat, sigma, walls, nstar, seed)
+    good = w.wdlb_batch_add(b, lat, sigma, walls, tau, g, n, u)
+    bad_n = n.copy()
+    bad_n[5, 3, 4] = np.nan
+    with pytest.raises(w.WDLBError) as ei:
+        w.wdlb_batch_add(b, lat, sigma, walls, tau, g, bad_n, u)
+    assert ei.value.status == 1
+    dense = np.full((8, 8, 8), 2.5 / 64)               # n* = 2.5: chi = 1.31
+    bad = w.wdlb_batch_add(b, (8, 8, 8), 4.0, False, 1.0, (0, 0, 0), dense)
+    w.wdlb_batch_residuals(b, 10)
+    w.wdlb_batch_step(b, 10)
+    _, st = w.wdlb_batch_residuals(b, 10)
+    assert st[bad] == 4 and st[good] == 0
+    f_b = w.wdlb_get_populations(w.wdlb_batch_context(b, good))
+    assert np.array_equal(f_b, alone(w, PORES[0], 10))
+    w.wdlb_batch_destroy(b)
