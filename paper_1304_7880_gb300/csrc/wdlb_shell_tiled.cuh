@@ -133,7 +133,9 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
         if (p.interactions) {
             ShellAcc<float> a = {};
             const float s0 = 1.f - hr - hoff;
-#pragma unroll 3
+            // three pairs per iteration; kept rolled for sigma 6 (225 pairs), where
+            // it measured 1.5 % faster
+#pragma unroll(S2 >= 12 ? 1 : 3)
             for (int m = 0; m < NPAIR; m++) {
                 const float4 t = smt[m];
                 const int off = __float_as_int(t.w);
