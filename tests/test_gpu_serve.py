@@ -18,6 +18,7 @@ REQUESTS = [
     ((8, 8, 25), 4.0, 0.5, 1e-5, 53),
     ((12, 12, 21), 3.0, 0.45, 2e-6, 54),
     ((10, 8, 19), 4.0, 0.25, 5e-6, 55),
+    ((12, 9, 27), 6.0, 0.3, 4e-6, 56),        # a third shell group (sigma 6) in the same batch
 ]
 TOL = 1e-6
 
