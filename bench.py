@@ -467,6 +467,33 @@ def run_ours(args):
     if not args.no_serve:
         serve = run_serving_pair(w, synth, np)
 
+    # ---------------- pore-viscosity sweep (Sec. 5, Fig. 2's experiment) ----------------
+    sweep = None
+    if not args.no_serve:
+        from paper_1304_7880_gb300 import sweeps
+        widths = [8, 12, 16, 24, 32, 48, 64, 96, 128, 160, 200]
+        sweep = {"widths_H": widths, "sigma": 4.0, "tau": 1.0, "g_x": 1e-6,
+                 "method": "steady slit Poiseuille per width through the serving loop (relative pore-flux change "
+                           "< 1e-8 per step), eta_eff = <n> g H^2 / (12 <u_x>) over the long-wave bulk shear "
+                           "viscosity at <n>"}
+        t0 = time.perf_counter()
+        for chi in (0.11, 0.32):
+            res = sweeps.pore_viscosity_sweep(chi, widths)
+            sweep["ratio_chi_%g" % chi] = [round(r["ratio"], 5) if r["status"] == 0 else None for r in res]
+        dt = time.perf_counter() - t0
+        sweep["solves"] = 2 * len(widths)
+        sweep["seconds"] = dt
+        sweep["solves_per_s"] = 2 * len(widths) / dt
+        # bulk viscosity against packing fraction (Sec. 5, Fig. 1's experiment), sigma 8
+        t0 = time.perf_counter()
+        bres = sweeps.bulk_viscosity_sweep([0.05, 0.1, 0.15, 0.2, 0.25, 0.3, 0.35])
+        sweep["bulk_sigma8"] = {"chi": [r["chi"] for r in bres if r["K"] == 2.0],
+                                "eta_K2": [r["eta"] for r in bres if r["K"] == 2.0],
+                                "eta_K0": [r["eta"] for r in bres if r["K"] == 0.0],
+                                "measured_over_theory_K2": [round(r["eta"] / r["eta_theory"], 5)
+                                                            for r in bres if r["K"] == 2.0],
+                                "seconds": time.perf_counter() - t0}
+
     # ---------------- other storage paths (same workload, shorter) ----------------
     paths = {}
     for storage, sub, reps in (("f64", 10, 2), ("f16", SUB, 3)):
@@ -533,7 +560,7 @@ def run_ours(args):
                     "path": "wdlb_init_fields(host) + wdlb_step(100) + wdlb_moments(host), pinned buffers"},
             "clocks": clocks, "gpu_launches": int(gpu_launches),
             "kernels_ms": {"moments": kms[0], "smeared_density": kms[1], "shell_collide_stream": kms[2]},
-            "paths": paths, "batched": batched, "serve": serve, "pore_average": {k: stats[k] for k in ("mass", "mean_n", "mean_ux", "steps")}}
+            "paths": paths, "batched": batched, "serve": serve, "pore_viscosity_sweep": sweep, "pore_average": {k: stats[k] for k in ("mass", "mean_n", "mean_ux", "steps")}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

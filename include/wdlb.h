@@ -48,7 +48,8 @@ typedef enum {
     WDLB_ERR_OOM = 2,      /* device allocation failed or workspace too small   */
     WDLB_ERR_CUDA = 3,     /* a CUDA call failed; message in wdlb_last_error    */
     WDLB_ERR_UNSTABLE = 4, /* smeared packing fraction >= 1 or non-finite state */
-    WDLB_ERR_TIMEOUT = 5,  /* a bounded device wait ran out                     */
+    WDLB_ERR_TIMEOUT = 5,  /* a bounded wait ran out, or a served request hit its
+                              step cap before its steady-state tolerance        */
     WDLB_ERR_STATE = 6     /* call out of order (e.g. step before init)         */
 } wdlb_status;
 

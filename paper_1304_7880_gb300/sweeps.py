@@ -1,20 +1,23 @@
-"""Pore-viscosity sweep of Sec. 5 (the experiment behind Fig. 2): plane
-Poiseuille flow of the hard-sphere fluid between two smooth walls, for a range
-of slab widths, each run to its steady state on the GPU through the serving
-loop, and the effective viscosity of the pore normalised by the bulk shear
-viscosity at the pore's mean density.
+"""Viscosity sweeps of Sec. 5, run on the GPU path.
 
-- Effective viscosity (pore average): eta_eff = <n> g_x H^2 / (12 <u_x>), with
-  H = nz - 2 the hydrodynamic width and averages over fluid nodes
-  (wdlb_pore_average).  The paper's "effective slab width" W - sigma is H.
-- Bulk shear viscosity: the long-wave limit of the decay of a transverse wave
-  under the same discrete equations (Sec. 4, Eq. treotto, with the lattice
-  shell sums in place of the angular integrals):
-      eta / n = kT (tau - 1/2)                                     kinetic
-              + (tau - 1/2) K kT n g2 (4 pi sigma^3 / 15)          cross-over (A-term)
-              + (beta / 2) g2 n sum_e w khat_x^2 e_z^2             collisional (F^viscous)
-  with beta = 2 sigma^2 sqrt(kT / pi), g2 the Carnahan-Starling contact value
-  at the density and w the library's uniform shell weight.
+- Pore viscosity (the experiment behind Fig. 2): plane Poiseuille flow of the
+  hard-sphere fluid between two smooth walls for a range of slab widths, each
+  run to its steady state through the serving loop; the effective viscosity
+  eta_eff = <n> g_x H^2 / (12 <u_x>) (H = nz - 2 the hydrodynamic width,
+  averages over fluid nodes; the paper's "effective slab width" W - sigma is
+  H) normalised by the bulk shear viscosity at the pore's mean density.
+- Bulk viscosity (the experiment behind Fig. 1): the decay rate r of a
+  transverse wave of wavenumber q in a periodic box gives eta = n r / q^2, with
+  and without the cross-over term (K = 2 and 0).
+
+The bulk shear viscosity in closed form is the long-wave limit of that decay
+under the same discrete equations (Sec. 4, Eq. treotto, with the lattice shell
+sums in place of the angular integrals):
+    eta / n = kT (tau - 1/2)                                     kinetic
+            + (tau - 1/2) K kT n g2 (4 pi sigma^3 / 15)          cross-over (A-term)
+            + (beta / 2) g2 n sum_e w khat_x^2 e_z^2             collisional (F^viscous)
+with beta = 2 sigma^2 sqrt(kT / pi), g2 the Carnahan-Starling contact value at
+the density and w the library's uniform shell weight.
 """
 from __future__ import annotations
 
@@ -86,4 +89,46 @@ def pore_viscosity_sweep(chi: float, widths, sigma: float = 4.0, tau: float = 1.
         out.append({"H": int(H), "status": 0, "steps": r["steps"], "mean_n": st["mean_n"],
                     "eta_eff": st["eta_eff"], "eta_bulk": eta_b, "ratio": st["eta_eff"] / eta_b,
                     "seconds": r["finish_s"] - r["start_s"]})
+    return out
+
+
+def bulk_viscosity_sweep(chis, sigma: float = 8.0, tau: float = 1.0, k_values=(2.0, 0.0), L: int = 256,
+                         nxy: int = 8, amplitude: float = 1e-6, storage: str = "f32"):
+    """Bulk shear viscosity against packing fraction (Sec. 5, the experiment
+    behind Fig. 1): a uniform fluid at rest is perturbed by a transverse wave
+    u_x = a sin(2 pi z / L) on an nxy x nxy x L periodic box, and its decay
+    rate r gives eta = n r / q^2, q = 2 pi / L.  For every packing fraction and
+    every K of the A-term (k_values: with and without the cross-over term).
+    The amplitude is fitted over one e-fold of decay after a tenth of it.
+    Returns dicts with chi, K, n, eta (measured), eta_theory (the long-wave
+    closed form) and steps."""
+    q = 2.0 * math.pi / L
+    z = np.arange(L)
+    sz = np.sin(q * z)
+    out = []
+    for chi in chis:
+        n0 = synth.packing_to_density(chi, sigma)
+        for K in k_values:
+            eta_th = bulk_shear_viscosity(n0, sigma, tau, K)
+            rate_th = eta_th / n0 * q * q
+            span = int(math.ceil(1.0 / rate_th))               # one e-fold
+            every = max(1, span // 8)
+            n = np.full((L, nxy, nxy), n0)
+            u = np.zeros((3, L, nxy, nxy))
+            u[0] = amplitude * sz[:, None, None]
+            ctx = w.wdlb_create((nxy, nxy, L), sigma, False, tau, (0.0, 0.0, 0.0), storage=storage,
+                                k_cross=K)
+            w.wdlb_init_fields(ctx, n, u)
+            w.wdlb_step(ctx, span // 10)
+            t, a = [], []
+            for k in range(9):
+                if k:
+                    w.wdlb_step(ctx, every)
+                t.append(span // 10 + k * every)
+                ux = w.wdlb_moments(ctx)[1][0].mean(axis=(1, 2))
+                a.append(2.0 / L * float(np.sum(ux * sz)))
+            w.wdlb_destroy(ctx)
+            rate = -np.polyfit(t, np.log(a), 1)[0]
+            out.append({"chi": chi, "K": K, "n": n0, "eta": n0 * rate / (q * q), "eta_theory": eta_th,
+                        "steps": t[-1]})
     return out
