@@ -30,6 +30,7 @@ _lib = None
 
 CLOSURES = {"CS": 0, "PY": 1, "ONE": 2}
 OMEGA_MODES = {"const": 0, "nbar": 1}
+SHELL_RULES = {"full": 0, "compact": 1}
 
 
 def build(force: bool = False) -> str:
@@ -51,7 +52,7 @@ def _load():
     lib = ctypes.CDLL(_LIB_PATH)
     D, I, L, P = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
     lib.wo_create.restype = P
-    lib.wo_create.argtypes = [I, I, I, I, D, D, D, D, D, I, I, D, D, I]
+    lib.wo_create.argtypes = [I, I, I, I, D, D, D, D, D, I, I, D, D, I, I]
     lib.wo_destroy.argtypes = [P]
     lib.wo_init.argtypes = [P, P, P]
     lib.wo_step.argtypes = [P, L]
@@ -72,6 +73,8 @@ def _load():
     lib.wo_ball.restype = I
     lib.wo_shell.argtypes = [D, P, I, P]
     lib.wo_shell.restype = I
+    lib.wo_shell_compact.argtypes = [D, P, P, I]
+    lib.wo_shell_compact.restype = I
     lib.wo_closure.argtypes = [I, D]
     lib.wo_closure.restype = D
     lib.wo_collide_node.argtypes = [P, P, P, D, D, P]
@@ -112,6 +115,21 @@ def shell(sigma: float):
     return e, w.value
 
 
+def shell_compact(sigma: float):
+    """Compact contact shell (a quadrature of this library; the paper's
+    integral over khat, Eq. campoc, with two or three cubic orbits of the shell
+    and one weight per orbit): vectors (m, 3) and weights (m,), or None when
+    no such rule exists at this sigma."""
+    lib = _load()
+    m = lib.wo_shell_compact(float(sigma), None, None, 0)
+    if m == 0:
+        return None
+    e = np.zeros((m, 3), dtype=np.int32)
+    w = np.zeros(m)
+    lib.wo_shell_compact(float(sigma), _ptr(e), _ptr(w), m)
+    return e, w
+
+
 def closure(kind: str, chi: float) -> float:
     """Homogeneous contact value g2(sigma+) at packing fraction chi (Sec. 3)."""
     return _load().wo_closure(CLOSURES[kind], float(chi))
@@ -132,7 +150,7 @@ class Oracle:
     """One lattice (bulk box or slit between walls at z = 0 and z = nz-1)."""
 
     def __init__(self, nx, ny, nz, walls, sigma, tau, g=(0.0, 0.0, 0.0), closure="CS",
-                 omega_mode="const", k_cross=2.0, n_ref=0.0, interactions=True):
+                 omega_mode="const", k_cross=2.0, n_ref=0.0, interactions=True, shell_rule="full"):
         self.lib = _load()
         self.shape = (int(nz), int(ny), int(nx))
         self.N = int(nx) * int(ny) * int(nz)
@@ -142,7 +160,7 @@ class Oracle:
         self.h = self.lib.wo_create(int(nx), int(ny), int(nz), int(bool(walls)), float(sigma), float(tau),
                                     self.g[0], self.g[1], self.g[2], CLOSURES[closure],
                                     OMEGA_MODES[omega_mode], float(k_cross), float(n_ref),
-                                    int(bool(interactions)))
+                                    int(bool(interactions)), SHELL_RULES[shell_rule])
         if not self.h:
             raise ValueError("oracle: invalid lattice parameters")
 

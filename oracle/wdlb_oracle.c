@@ -29,6 +29,18 @@
  *       (sigma-1/2)^2 < |e|^2 <= (sigma+1/2)^2 with one uniform weight chosen so
  *       that sigma^2 * sum_e w khat_z e_z = 4 pi sigma^3 / 3 (the discrete
  *       virial coefficient then equals b = 2 pi sigma^3 / 3 exactly).
+ *   R4c shell rule COMPACT (a quadrature of this library; the paper gives
+ *       none): the union of two or three cubic orbits of the R4 shell, one
+ *       weight per orbit, the weights fixed by three moment conditions,
+ *         sigma^2 sum_e w_e khat_z e_z   = 4 pi sigma^3 / 3   (virial coefficient b)
+ *         sum_e w_e khat_x^2 e_z^2       = 4 pi sigma^2 / 15  (continuum value of
+ *                                          the collisional-viscosity moment)
+ *         sum_e w_e khat_z^2 e_z^2       = 3 sum_e w_e khat_x^2 e_z^2  (isotropic
+ *                                          fourth moment),
+ *       every weight positive (> 1e-3 of the largest); of all such unions the
+ *       one with the fewest vectors, then the smallest sum over its vectors of
+ *       (|e|^2 - sigma^2)^2, then the first in orbit order (orbits ordered by
+ *       |e|^2, then by their sorted components).
  *   R5  the SMDB source carries K times the traceless part of A in its second
  *       moment (K = 2 reproduces Eq. extrapressure).
  *   R6  lattice units a = dt = m = 1, k_B T = c_s^2 = 1/3.
@@ -147,6 +159,177 @@ int wo_shell(double sigma, int *e_out, int cap, double *w_out)
     return m;
 }
 
+/* Compact contact shell (R4c).  Orbits of the cubic group: the distinct
+ * sign changes and permutations of (a, b, c), 0 <= a <= b <= c.              */
+#define WO_MAX_ORBITS 96
+
+typedef struct {
+    int a, b, c, r2, size;
+    double m1;      /* sum over the orbit of khat_z e_z = e_z^2 / |e|              */
+    double vc;      /* sum of khat_x^2 e_z^2 = e_x^2 e_z^2 / |e|^2                 */
+    double an;      /* sum of khat_z^2 e_z^2 - 3 khat_x^2 e_z^2                     */
+} wo_orbit;
+
+static int orbit_members(int a, int b, int c, int out[48][3])
+{
+    static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    const int v[3] = {a, b, c};
+    int m = 0;
+    for (int p = 0; p < 6; p++)
+        for (int sg = 0; sg < 8; sg++) {
+            int e[3];
+            for (int d = 0; d < 3; d++) e[d] = ((sg >> d) & 1) ? -v[perm[p][d]] : v[perm[p][d]];
+            int dup = 0;
+            for (int k = 0; k < m && !dup; k++)
+                dup = out[k][0] == e[0] && out[k][1] == e[1] && out[k][2] == e[2];
+            if (!dup) {
+                out[m][0] = e[0]; out[m][1] = e[1]; out[m][2] = e[2];
+                m++;
+            }
+        }
+    return m;
+}
+
+static int orbit_less(const wo_orbit *p, const wo_orbit *q)
+{
+    if (p->r2 != q->r2) return p->r2 < q->r2;
+    if (p->a != q->a) return p->a < q->a;
+    if (p->b != q->b) return p->b < q->b;
+    return p->c < q->c;
+}
+
+/* Weights of the orbits idx[0..k-1] (k = 2 or 3) solving the three moment
+ * conditions of R4c: Cramer's rule for k = 3, the normal equations for k = 2
+ * (then the residual of each condition must vanish).  Returns 1 with w[] if
+ * the conditions hold and every weight is positive. */
+static int compact_weights(const wo_orbit *o, const int *idx, int k, double sigma, double *w)
+{
+    double A[3][3], rhs[3] = {4.0 * M_PI * sigma / 3.0, 4.0 * M_PI * sigma * sigma / 15.0, 0.0};
+    for (int j = 0; j < k; j++) {
+        A[0][j] = o[idx[j]].m1;
+        A[1][j] = o[idx[j]].vc;
+        A[2][j] = o[idx[j]].an;
+    }
+    if (k == 3) {
+        double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1])
+                   - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
+                   + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+        double scale = 1.0;
+        for (int j = 0; j < 3; j++)
+            scale *= sqrt(A[0][j] * A[0][j] + A[1][j] * A[1][j] + A[2][j] * A[2][j]);
+        if (fabs(det) <= 1e-12 * scale) return 0;
+        for (int j = 0; j < 3; j++) {
+            double M[3][3];
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) M[r][c] = (c == j) ? rhs[r] : A[r][c];
+            double dj = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1])
+                      - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])
+                      + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+            w[j] = dj / det;
+        }
+    } else {
+        double g00 = 0, g01 = 0, g11 = 0, b0 = 0, b1 = 0;
+        for (int r = 0; r < 3; r++) {
+            g00 += A[r][0] * A[r][0];
+            g01 += A[r][0] * A[r][1];
+            g11 += A[r][1] * A[r][1];
+            b0 += A[r][0] * rhs[r];
+            b1 += A[r][1] * rhs[r];
+        }
+        double det = g00 * g11 - g01 * g01;
+        if (fabs(det) <= 1e-12 * g00 * g11) return 0;
+        w[0] = (b0 * g11 - b1 * g01) / det;
+        w[1] = (g00 * b1 - g01 * b0) / det;
+    }
+    double wmax = 0.0;
+    for (int j = 0; j < k; j++) wmax = w[j] > wmax ? w[j] : wmax;
+    for (int j = 0; j < k; j++)
+        if (!(w[j] > 1e-3 * wmax)) return 0;
+    for (int r = 0; r < 3; r++) {
+        double lhs = 0.0, mag = fabs(rhs[r]);
+        for (int j = 0; j < k; j++) {
+            lhs += A[r][j] * w[j];
+            mag += fabs(A[r][j] * w[j]);
+        }
+        if (fabs(lhs - rhs[r]) > 1e-9 * mag) return 0;
+    }
+    return 1;
+}
+
+/* The compact shell of R4c: its vectors and their weights.  Returns the
+ * vector count, 0 if no union of two or three orbits satisfies R4c. */
+int wo_shell_compact(double sigma, int *e_out, double *w_out, int cap)
+{
+    const int R = (int)floor(sigma + 0.5);
+    const double lo = (sigma - 0.5) * (sigma - 0.5), hi = (sigma + 0.5) * (sigma + 0.5);
+    wo_orbit o[WO_MAX_ORBITS];
+    int no = 0;
+    int mem[48][3];
+    for (int c = 0; c <= R; c++)
+        for (int b = 0; b <= c; b++)
+            for (int a = 0; a <= b; a++) {
+                int r2 = a * a + b * b + c * c;
+                if (!((double)r2 > lo && (double)r2 <= hi) || no >= WO_MAX_ORBITS) continue;
+                wo_orbit t = {a, b, c, r2, 0, 0.0, 0.0, 0.0};
+                t.size = orbit_members(a, b, c, mem);
+                for (int m = 0; m < t.size; m++) {
+                    double ex = mem[m][0], ez = mem[m][2], len2 = (double)r2;
+                    t.m1 += ez * ez / sqrt(len2);
+                    t.vc += ex * ex * ez * ez / len2;
+                    t.an += (ez * ez * ez * ez - 3.0 * ex * ex * ez * ez) / len2;
+                }
+                int pos = no++;                        /* insertion in orbit order */
+                while (pos > 0 && orbit_less(&t, &o[pos - 1])) {
+                    o[pos] = o[pos - 1];
+                    pos--;
+                }
+                o[pos] = t;
+            }
+    int best[3] = {-1, -1, -1}, bestk = 0, bestn = 0;
+    double bestw[3] = {0, 0, 0}, bests = 0.0;
+    for (int k = 2; k <= 3; k++) {
+        int idx[3];
+        for (idx[0] = 0; idx[0] < no; idx[0]++)
+            for (idx[1] = idx[0] + 1; idx[1] < no; idx[1]++)
+                for (idx[2] = (k == 3 ? idx[1] + 1 : no); idx[2] <= (k == 3 ? no - 1 : no); idx[2]++) {
+                    double w[3];
+                    if (!compact_weights(o, idx, k, sigma, w)) continue;
+                    int n = 0;
+                    double spread = 0.0;
+                    for (int j = 0; j < k; j++) {
+                        double d = (double)o[idx[j]].r2 - sigma * sigma;
+                        n += o[idx[j]].size;
+                        spread += o[idx[j]].size * d * d;
+                    }
+                    if (bestk == 0 || n < bestn || (n == bestn && spread < bests - 1e-9 * (1.0 + bests))) {
+                        bestk = k; bestn = n; bests = spread;
+                        for (int j = 0; j < k; j++) { best[j] = idx[j]; bestw[j] = w[j]; }
+                    }
+                }
+    }
+    if (bestk == 0) return 0;
+    int m = 0;
+    for (int z = -R; z <= R; z++)
+        for (int y = -R; y <= R; y++)
+            for (int x = -R; x <= R; x++) {
+                int v[3] = {abs(x), abs(y), abs(z)};
+                for (int p = 0; p < 2; p++)             /* sort |components| */
+                    for (int q = 0; q < 2 - p; q++)
+                        if (v[q] > v[q + 1]) { int t = v[q]; v[q] = v[q + 1]; v[q + 1] = t; }
+                for (int j = 0; j < bestk; j++) {
+                    const wo_orbit *t = &o[best[j]];
+                    if (v[0] == t->a && v[1] == t->b && v[2] == t->c) {
+                        if (m < cap) {
+                            if (e_out) { e_out[3 * m] = x; e_out[3 * m + 1] = y; e_out[3 * m + 2] = z; }
+                            if (w_out) w_out[m] = bestw[j];
+                        }
+                        m++;
+                    }
+                }
+            }
+    return m;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Contact value of the homogeneous pair distribution (R1), chi = pi n s^3/6 */
 /* ---------------------------------------------------------------------- */
@@ -167,7 +350,8 @@ typedef struct {
     int closure, omega_mode, interactions;
     int nball, nshell;
     int *ball, *shell;
-    double wshell;
+    double *wvec;                      /* weight of each shell vector (R4 or R4c) */
+    int shell_rule;                    /* 0: R4 (full shell), 1: R4c (compact) */
     double *f, *fnew;                  /* [Q][N] */
     double *n, *j, *us;                /* n[N], j[3][N], field velocity v[3][N] */
     double *nbar;                      /* [N] */
@@ -203,17 +387,19 @@ static long neighbour(const wo_state *s, int x, int y, int z, int dx, int dy, in
 void wo_destroy(wo_state *s)
 {
     if (!s) return;
-    free(s->ball); free(s->shell); free(s->f); free(s->fnew); free(s->n); free(s->j);
+    free(s->ball); free(s->shell); free(s->wvec); free(s->f); free(s->fnew); free(s->n); free(s->j);
     free(s->us); free(s->nbar); free(s->Cf); free(s->A); free(s->Cprev); free(s->Tprev); free(s->vprev); free(s->Tcur);
     free(s);
 }
 
 wo_state *wo_create(int nx, int ny, int nz, int walls, double sigma, double tau,
                     double gx, double gy, double gz, int closure, int omega_mode,
-                    double k_cross, double n_ref, int interactions)
+                    double k_cross, double n_ref, int interactions, int shell_rule)
 {
     build_d3q19();
     if (nx < 1 || ny < 1 || nz < 1 || (walls && nz < 3) || sigma < 1.0 || tau <= 0.5)
+        return NULL;
+    if (shell_rule != 0 && (shell_rule != 1 || wo_shell_compact(sigma, NULL, NULL, 0) == 0))
         return NULL;
     wo_state *s = (wo_state *)calloc(1, sizeof(wo_state));
     s->nx = nx; s->ny = ny; s->nz = nz; s->walls = walls;
@@ -224,9 +410,20 @@ wo_state *wo_create(int nx, int ny, int nz, int walls, double sigma, double tau,
     s->nball = wo_ball(sigma, NULL, 0);
     s->ball = (int *)malloc(sizeof(int) * 3 * s->nball);
     wo_ball(sigma, s->ball, s->nball);
-    s->nshell = wo_shell(sigma, NULL, 0, &s->wshell);
-    s->shell = (int *)malloc(sizeof(int) * 3 * s->nshell);
-    wo_shell(sigma, s->shell, s->nshell, NULL);
+    s->shell_rule = shell_rule;
+    if (shell_rule == 0) {
+        double w;
+        s->nshell = wo_shell(sigma, NULL, 0, &w);
+        s->shell = (int *)malloc(sizeof(int) * 3 * s->nshell);
+        s->wvec = (double *)malloc(sizeof(double) * s->nshell);
+        wo_shell(sigma, s->shell, s->nshell, NULL);
+        for (int m = 0; m < s->nshell; m++) s->wvec[m] = w;
+    } else {
+        s->nshell = wo_shell_compact(sigma, NULL, NULL, 0);
+        s->shell = (int *)malloc(sizeof(int) * 3 * s->nshell);
+        s->wvec = (double *)malloc(sizeof(double) * s->nshell);
+        wo_shell_compact(sigma, s->shell, s->wvec, s->nshell);
+    }
     long N = s->N;
     s->f = (double *)calloc((size_t)Q * N, sizeof(double));
     s->fnew = (double *)calloc((size_t)Q * N, sizeof(double));
@@ -353,7 +550,7 @@ static void shell_fields(wo_state *s)
                     double kh[3] = {ex / len, ey / len, ez / len};
                     double chi = chi_of_n * 0.5 * (s->nbar[i] + s->nbar[k]);
                     if (chi >= 1.0) s->unstable = 1;
-                    double wgn = s->wshell * wo_closure(s->closure, chi) * s->n[k];
+                    double wgn = s->wvec[m] * wo_closure(s->closure, chi) * s->n[k];
                     double du[3];
                     for (int d = 0; d < 3; d++) du[d] = s->us[d * N + k] - s->us[d * N + i];
                     double kdu = kh[0] * du[0] + kh[1] * du[1] + kh[2] * du[2];
