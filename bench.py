@@ -61,6 +61,8 @@ def shell_size(sigma):
 # difference 3, khat.dv and q khat.dv 6, the F^mf, F^viscous and A sums 36,
 # t 1), plus 475 for moments, collision and the force terms.
 FLOPS_PER_PAIR = 52
+# the compact shell's per-vector weight: three more multiplies per (+e, -e) pair
+FLOPS_PER_PAIR_WEIGHTED = FLOPS_PER_PAIR + 1.5
 FLOPS_COLLIDE = 475
 # Algorithmic HBM bytes per node update: read and write 19 populations.
 BYTES_PER_NODE = {"f64": 19 * 2 * 8, "f32": 19 * 2 * 4, "f16": 19 * 2 * 2}
@@ -360,8 +362,9 @@ def run_ours(args):
     N = L ** 3
     shape = (p["nx"], p["ny"], p["nz"])
 
-    def make(storage):
-        ctx = w.wdlb_create(shape, p["sigma"], p["walls"], p["tau"], p["g"], storage=storage, tile=args.tile)
+    def make(storage, shell_rule="full"):
+        ctx = w.wdlb_create(shape, p["sigma"], p["walls"], p["tau"], p["g"], storage=storage, tile=args.tile,
+                            shell_rule=shell_rule)
         d_n = torch.from_numpy(n_h).cuda()
         d_u = torch.from_numpy(u_h).cuda()
         torch.cuda.synchronize()
@@ -493,11 +496,20 @@ def run_ours(args):
                                 "measured_over_theory_K2": [round(r["eta"] / r["eta_theory"], 5)
                                                             for r in bres if r["K"] == 2.0],
                                 "seconds": time.perf_counter() - t0}
+        t0 = time.perf_counter()
+        cres = sweeps.bulk_viscosity_sweep([0.05, 0.1, 0.15, 0.2, 0.25, 0.3, 0.35], shell_rule="compact")
+        sweep["bulk_sigma8_compact_shell"] = {
+            "eta_K2": [r["eta"] for r in cres if r["K"] == 2.0],
+            "eta_K0": [r["eta"] for r in cres if r["K"] == 0.0],
+            "measured_over_theory_K2": [round(r["eta"] / r["eta_theory"], 5) for r in cres if r["K"] == 2.0],
+            "over_full_shell_K2": [round(c["eta"] / f["eta"], 5) for c, f in zip(cres, bres) if c["K"] == 2.0],
+            "seconds": time.perf_counter() - t0}
 
-    # ---------------- other storage paths (same workload, shorter) ----------------
+    # ---------------- other storage paths and the compact shell (same workload, shorter) ----------------
     paths = {}
-    for storage, sub, reps in (("f64", 10, 2), ("f16", SUB, 3)):
-        c2 = make(storage)
+    for name, storage, rule, sub, reps in (("f64", "f64", "full", 10, 2), ("f16", "f16", "full", SUB, 3),
+                                           ("f32_compact_shell", "f32", "compact", SUB, 3)):
+        c2 = make(storage, rule)
         w.wdlb_profile_step(c2, sub)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -512,9 +524,19 @@ def run_ours(args):
         torch.cuda.synchronize()
         t = max_over_ranks(a.elapsed_time(b))
         mlups = job_mlups(world, N, sub * reps, t * 1e-3)
-        paths[storage] = {"value": mlups, "unit": UNIT, "kernels_ms": pk,
-                          "hbm_frac_of_measured": mlups * 1e6 * BYTES_PER_NODE[storage] / 1e9
-                          / measured_peaks()[0]["hbm_gbs"]}
+        paths[name] = {"value": mlups, "unit": UNIT, "kernels_ms": pk,
+                       "hbm_frac_of_measured": mlups * 1e6 * BYTES_PER_NODE[storage] / 1e9
+                       / measured_peaks()[0]["hbm_gbs"]}
+        if rule == "compact":
+            ns = len(w.wdlb_shell_table(SIGMA, "compact")[1])
+            fl = ns * FLOPS_PER_PAIR_WEIGHTED + FLOPS_COLLIDE
+            alu = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+            tf = fl * N / (pk[2] * 1e-3) / 1e12
+            paths[name].update({"shell_vectors": ns, "full_shell_vectors": shell_size(SIGMA),
+                                "tile_shape": w.wdlb_tile_info(c2)[1], "flops_per_node": fl,
+                                "shell_kernel_alu_frac": tf / alu, "shell_kernel_tflops": tf,
+                                "shell_kernel_hbm_frac_of_measured": BYTES_PER_NODE[storage] * N / (pk[2] * 1e-3)
+                                / 1e9 / measured_peaks()[0]["hbm_gbs"]})
         w.wdlb_destroy(c2)
 
     if rank != 0:

@@ -71,6 +71,25 @@ enum { WDLB_OMEGA_CONST = 0, WDLB_OMEGA_NBAR = 1 };
  * rest state w_q n_ref (FP32 arithmetic), FP16 relative deviation
  * f_q / (w_q n_ref) - 1 (FP32 arithmetic). */
 enum { WDLB_STORE_F64 = 0, WDLB_STORE_F32 = 1, WDLB_STORE_F16 = 2 };
+/* Quadrature of the integral over khat in Eq. campoc (the paper leaves the
+ * discrete form open):
+ *   FULL     every lattice vector with (sigma-1/2)^2 < |e|^2 <= (sigma+1/2)^2
+ *            and one uniform weight w, sigma^2 sum_e w e_z^2/|e| = 4 pi sigma^3/3
+ *            (the discrete virial coefficient is b = 2 pi sigma^3/3 exactly);
+ *   COMPACT  two or three orbits of the cubic group inside that shell, one
+ *            weight per orbit, fixed by the same virial condition, by
+ *            sum_e w_e khat_x^2 e_z^2 = 4 pi sigma^2/15 (the continuum value of
+ *            the moment behind the collisional viscosity) and by
+ *            sum_e w_e khat_z^2 e_z^2 = 3 sum_e w_e khat_x^2 e_z^2 (isotropic
+ *            fourth moment), every weight positive; of all such unions the one
+ *            with the fewest vectors (26 to 42 for sigma 3 to 8, against 98 to
+ *            762), then the smallest sum of (|e|^2 - sigma^2)^2, then the first
+ *            in orbit order (|e|^2, then sorted components).  No such union
+ *            exists below sigma = 1.55 or for 2.25 <= sigma <= 2.3: wdlb_create
+ *            then fails with WDLB_ERR_ARG.  The compact shell changes the
+ *            discrete equations (not the equation of state or the long-wave
+ *            shear viscosity, which it reproduces at the continuum values). */
+enum { WDLB_SHELL_FULL = 0, WDLB_SHELL_COMPACT = 1 };
 
 typedef struct {
     int32_t closure;          /* WDLB_CLOSURE_*, default CS                          */
@@ -94,7 +113,9 @@ typedef struct {
                                  256 threads (WDLB_TILE_*)                          */
     int32_t autotune;         /* with tile = -1: 1 (default) time the tile variants on
                                  a scratch lattice the first time a (storage, sigma,
-                                 walls, nz) key is seen; 0 use the built-in table    */
+                                 walls, nz, shell rule) key is seen; 0 use the
+                                 built-in table                                     */
+    int32_t shell_rule;       /* WDLB_SHELL_*, default FULL                          */
 } wdlb_options;
 
 enum { WDLB_TILE_AUTO = -1, WDLB_TILE_8x8x8 = 0, WDLB_TILE_8x8x8_WIDE = 1, WDLB_TILE_8x8x4 = 2 };
@@ -163,8 +184,9 @@ wdlb_status wdlb_get_populations(wdlb_ctx *ctx, double *f);
  * with n - n_off), C_prev, t_prev, the reference density and the step count;
  * restoring it continues the run bit for bit.  The buffer is an opaque host
  * blob of wdlb_state_bytes bytes, caller-owned, valid for a context with the
- * same lattice, walls, sigma, tau and storage (WDLB_ERR_ARG otherwise, and
- * for a buffer that is too small or not a saved state).  Synchronous. */
+ * same lattice, walls, sigma, tau, storage and shell rule (WDLB_ERR_ARG
+ * otherwise, and for a buffer that is too small or not a saved state).
+ * Synchronous. */
 wdlb_status wdlb_state_bytes(const wdlb_ctx *ctx, uint64_t *bytes);
 wdlb_status wdlb_save_state(wdlb_ctx *ctx, void *host, uint64_t bytes);
 wdlb_status wdlb_load_state(wdlb_ctx *ctx, const void *host, uint64_t bytes);
@@ -201,6 +223,13 @@ wdlb_status wdlb_run_steady(wdlb_ctx *ctx, double tol, int32_t check_every, int6
 wdlb_status wdlb_velocity_set(int32_t *c, double *w);
 wdlb_status wdlb_stencil(double sigma, int32_t which, int32_t *vecs, int32_t cap,
                          int32_t *count, double *weight);
+/* The contact shell of a quadrature rule (WDLB_SHELL_*) with the weight of
+ * every vector: writes up to cap vectors (3 int32 each, +e and -e adjacent)
+ * into vecs and their weights into weights (either may be NULL) and the full
+ * count into *count.  WDLB_ERR_ARG if sigma is outside [1, 8], the rule is
+ * unknown or it has no shell at this sigma.  Host only, no GPU needed. */
+wdlb_status wdlb_shell_table(double sigma, int32_t rule, int32_t *vecs, double *weights, int32_t cap,
+                             int32_t *count);
 
 /* Advance nsteps (>= 1) like wdlb_step, but launch the three kernels of each
  * step one by one with CUDA events around each on the context stream, and
@@ -215,7 +244,7 @@ wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3]);
  * fastest depends on sigma (shared memory per block, hence blocks per SM) and
  * on nz (z padding of the bricks in thin slits).  Contexts created with
  * tile = -1 take the shape from a process-wide table keyed by (storage,
- * sigma, walls, nz).  A missing key is filled by timing every shape on a
+ * sigma, walls, nz, shell rule).  A missing key is filled by timing every shape on a
  * scratch lattice of that key (nz as given, a square cross-section of about
  * 2^20 / nz nodes so that the kernel fills the GPU as a batch does; uniform
  * density; six steps after two warm-up steps) when autotune = 1, else from a
@@ -348,8 +377,8 @@ void wdlb_server_destroy(wdlb_server *s);
  * state at rest with respect to its own history -- the smeared density nbar,
  * C (Eq. campoc) and A (Eq. campod) with the neighbours' velocity u -- from
  * device arrays n (N doubles) and u (3N doubles), into device arrays nbar (N,
- * may be NULL), C (3N) and A (6N: xx, yy, zz, xy, xz, yz), FP32 arithmetic.
- * Solid nodes (walls) report 0.
+ * may be NULL), C (3N) and A (6N: xx, yy, zz, xy, xz, yz), FP32 arithmetic,
+ * with the full contact shell (WDLB_SHELL_FULL).  Solid nodes (walls) report 0.
  *
  * Its scratch is one file-scope __device__ array of fixed size (about 5 MiB:
  * the field arrays for WDLB_STATIC_MAX_NODES nodes, the stencil tables and a

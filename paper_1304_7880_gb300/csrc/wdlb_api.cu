@@ -35,7 +35,8 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct Tables {
     std::vector<int> ball;    // 3 per vector
     std::vector<int> shell;   // 3 per vector, +e and -e adjacent
-    double wshell = 0.0;
+    std::vector<double> wvec; // weight of each shell vector
+    double wshell = 0.0;      // uniform weight in the kernels (1 for the compact shell)
 };
 
 struct Layout {
@@ -169,6 +170,12 @@ wdlb_status validate(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_o
         if (opt->storage < 0 || opt->storage > 2) return WDLB_ERR_ARG;
         if (!(opt->n_ref >= 0.0) || !std::isfinite(opt->k_cross)) return WDLB_ERR_ARG;
         if (opt->tile < -1 || opt->tile > 2 || opt->autotune < 0 || opt->autotune > 1) return WDLB_ERR_ARG;
+        if (opt->shell_rule < 0 || opt->shell_rule > 1) return WDLB_ERR_ARG;
+        if (opt->shell_rule == WDLB_SHELL_COMPACT) {
+            std::vector<int> v;
+            std::vector<double> w;
+            if (!build_shell_compact(sigma, v, w)) return WDLB_ERR_ARG;
+        }
     }
     return WDLB_OK;
 }
@@ -194,6 +201,7 @@ void set_params(wdlb_ctx *ctx)
     p.nshell = (int)(ctx->tab.shell.size() / 3);
     p.nball = (int)(ctx->tab.ball.size() / 3);
     p.closure = ctx->opt.closure;
+    p.shell_rule = ctx->opt.shell_rule;
     p.omega_mode = ctx->opt.omega_mode;
     p.interactions = ctx->opt.interactions ? 1 : 0;
     for (int d = 0; d < 3; d++) p.g[d] = ctx->g[d];
@@ -281,6 +289,7 @@ cudaError_t upload_step_tables(wdlb_ctx *ctx)
     G.tiled = p.tiled;
     G.closure = p.closure;
     G.tile = p.tiled ? p.tile : -1;
+    G.rule = p.shell_rule;
     G.items = dit + items.size();
     if (p.tiled)
         bricks(tile_depth(p.tile));
@@ -374,15 +383,16 @@ wdlb_status stats(wdlb_ctx *ctx, int update_snap, double r[6])
 namespace {
 
 // ---------------------------------------------------------------------------
-// Tile autotuner: a process-wide table (storage, 2 sigma, walls, nz) -> tile
+// Tile autotuner: a process-wide table (storage, 2 sigma, walls, nz, shell
+// rule) -> tile
 // shape of the tiled shell kernel, filled on first use by timing every shape
 // on a scratch lattice of the key, or from the built-in table.
 // ---------------------------------------------------------------------------
 struct TuneKey {
-    int storage, s2, walls, nz;
+    int storage, s2, walls, nz, rule;
     bool operator<(const TuneKey &o) const
     {
-        return std::make_tuple(storage, s2, walls, nz) < std::make_tuple(o.storage, o.s2, o.walls, o.nz);
+        return std::make_tuple(storage, s2, walls, nz, rule) < std::make_tuple(o.storage, o.s2, o.walls, o.nz, o.rule);
     }
 };
 
@@ -457,7 +467,7 @@ int choose_tile(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_option
 {
     if (!tiled_applies(lat, sigma, o)) return WDLB_TILE_8x8x8;
     if (o.tile >= 0) return o.tile;
-    const TuneKey key{o.storage, two_sigma(sigma), walls, lat.nz};
+    const TuneKey key{o.storage, two_sigma(sigma), walls, lat.nz, o.shell_rule};
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) return it->second;
@@ -502,7 +512,7 @@ wdlb_status wdlb_workspace_size(wdlb_lattice lat, double sigma, int32_t walls, c
     if (s != WDLB_OK) return s;
     Tables t;
     build_ball(sigma, t.ball);
-    build_shell(sigma, t.shell, &t.wshell);
+    build_shell_rule(sigma, o.shell_rule, t.shell, t.wvec);
     long long N = (long long)lat.nx * lat.ny * lat.nz;
     long long Npad = (N + 63) / 64 * 64;
     *bytes = layout_for(lat, N, Npad, o.storage, (int)t.shell.size() / 3, (int)t.ball.size() / 3).total;
@@ -536,7 +546,8 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
     ctx->N = (long long)lat.nx * lat.ny * lat.nz;
     ctx->Npad = (ctx->N + 63) / 64 * 64;
     build_ball(sigma, ctx->tab.ball);
-    build_shell(sigma, ctx->tab.shell, &ctx->tab.wshell);
+    build_shell_rule(sigma, o.shell_rule, ctx->tab.shell, ctx->tab.wvec);
+    ctx->tab.wshell = o.shell_rule == WDLB_SHELL_COMPACT ? 1.0 : ctx->tab.wvec[0];
     ctx->L = &launchers_for(o.storage);
     set_params(ctx);
     ctx->kp.tile = choose_tile(lat, sigma, walls, o);
@@ -599,7 +610,7 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
         int x = ctx->tab.shell[3 * m], y = ctx->tab.shell[3 * m + 1], z = ctx->tab.shell[3 * m + 2];
         se[m] = make_int4(x, y, z, 0);
         double len = std::sqrt(double(x * x + y * y + z * z));
-        double k[4] = {x / len, y / len, z / len, 0.0};
+        double k[4] = {x / len, y / len, z / len, o.shell_rule == WDLB_SHELL_COMPACT ? ctx->tab.wvec[m] : 0.0};
         for (int c = 0; c < 4; c++) {
             kd[4 * m + c] = k[c];
             kf[4 * m + c] = float(k[c]);
@@ -823,6 +834,24 @@ wdlb_status wdlb_stencil(double sigma, int32_t which, int32_t *vecs, int32_t cap
     return WDLB_OK;
 }
 
+wdlb_status wdlb_shell_table(double sigma, int32_t rule, int32_t *vecs, double *weights, int32_t cap,
+                             int32_t *count)
+{
+    if (!(sigma >= 1.0 && sigma <= 8.0) || (rule != WDLB_SHELL_FULL && rule != WDLB_SHELL_COMPACT) || cap < 0)
+        return WDLB_ERR_ARG;
+    std::vector<int> v;
+    std::vector<double> w;
+    if (!build_shell_rule(sigma, rule, v, w)) return WDLB_ERR_ARG;
+    const int m = (int)w.size();
+    for (int k = 0; k < std::min(m, (int)cap); k++) {
+        if (vecs)
+            for (int d = 0; d < 3; d++) vecs[3 * k + d] = v[3 * k + d];
+        if (weights) weights[k] = w[k];
+    }
+    if (count) *count = m;
+    return WDLB_OK;
+}
+
 wdlb_status wdlb_profile_step(wdlb_ctx *ctx, int64_t nsteps, double ms[3])
 {
     if (!ctx || !ms) return ctx ? fail(ctx, WDLB_ERR_ARG, "ms is NULL") : WDLB_ERR_ARG;
@@ -863,7 +892,7 @@ namespace {
 
 struct StateHeader {
     uint64_t magic;
-    int32_t version, storage, nx, ny, nz, walls;
+    int32_t version, storage, nx, ny, nz, walls, shell_rule;
     int64_t N, steps;
     double sigma, tau, n_ref;
 };
@@ -899,8 +928,8 @@ wdlb_status wdlb_save_state(wdlb_ctx *ctx, void *host, uint64_t bytes)
     wdlb_state_bytes(ctx, &need);
     if (bytes < need) return fail(ctx, WDLB_ERR_ARG, "state buffer too small (%llu < %llu)",
                                   (unsigned long long)bytes, (unsigned long long)need);
-    StateHeader h{kStateMagic, 1, ctx->opt.storage, ctx->lat.nx, ctx->lat.ny, ctx->lat.nz, ctx->walls,
-                  ctx->N, ctx->steps, ctx->sigma, ctx->tau, ctx->kp.n_off};
+    StateHeader h{kStateMagic, 2, ctx->opt.storage, ctx->lat.nx, ctx->lat.ny, ctx->lat.nz, ctx->walls,
+                  ctx->opt.shell_rule, ctx->N, ctx->steps, ctx->sigma, ctx->tau, ctx->kp.n_off};
     char *out = static_cast<char *>(host);
     std::memcpy(out, &h, sizeof(h));
     size_t off = sizeof(h);
@@ -920,9 +949,10 @@ wdlb_status wdlb_load_state(wdlb_ctx *ctx, const void *host, uint64_t bytes)
     if (bytes < need) return fail(ctx, WDLB_ERR_ARG, "state buffer too small");
     StateHeader h;
     std::memcpy(&h, host, sizeof(h));
-    if (h.magic != kStateMagic || h.version != 1) return fail(ctx, WDLB_ERR_ARG, "not a saved state");
+    if (h.magic != kStateMagic || h.version != 2) return fail(ctx, WDLB_ERR_ARG, "not a saved state");
     if (h.storage != ctx->opt.storage || h.nx != ctx->lat.nx || h.ny != ctx->lat.ny || h.nz != ctx->lat.nz ||
-        h.walls != ctx->walls || h.N != ctx->N || h.sigma != ctx->sigma || h.tau != ctx->tau)
+        h.walls != ctx->walls || h.shell_rule != ctx->opt.shell_rule || h.N != ctx->N || h.sigma != ctx->sigma ||
+        h.tau != ctx->tau)
         return fail(ctx, WDLB_ERR_ARG, "saved state belongs to another lattice or configuration");
     set_reference(ctx, h.n_ref);
     drop_graphs(ctx);
@@ -957,7 +987,7 @@ wdlb_status wdlb_autotune(wdlb_lattice lat, double sigma, int32_t walls, const w
     double t[3];
     wdlb_status s = probe_tiles(lat, sigma, walls, o, &b, t);
     if (s != WDLB_OK) return s;
-    g_tune[TuneKey{o.storage, two_sigma(sigma), walls, lat.nz}] = b;
+    g_tune[TuneKey{o.storage, two_sigma(sigma), walls, lat.nz, o.shell_rule}] = b;
     if (best) *best = b;
     if (ms)
         for (int v = 0; v < 3; v++) ms[v] = t[v];
@@ -1102,11 +1132,11 @@ wdlb_status batch_build(wdlb_batch *b)
     std::vector<BatchItem> node_items, ball_items, ball_node_items;
     size_t ball_smem = 0;
     struct Key {
-        int s2, walls, tiled, closure, tile;
+        int s2, walls, tiled, closure, tile, rule;
         bool operator<(const Key &o) const
         {
-            return std::make_tuple(s2, walls, tiled, closure, tile) <
-                   std::make_tuple(o.s2, o.walls, o.tiled, o.closure, o.tile);
+            return std::make_tuple(s2, walls, tiled, closure, tile, rule) <
+                   std::make_tuple(o.s2, o.walls, o.tiled, o.closure, o.tile, o.rule);
         }
     };
     std::map<Key, std::vector<BatchItem>> groups;
@@ -1129,7 +1159,8 @@ wdlb_status batch_build(wdlb_batch *b)
         } else {
             for (int k = 0; k < (N + 255) / 256; k++) ball_node_items.push_back(BatchItem{s, k, 0, 0});
         }
-        Key key{c->kp.tiled ? c->kp.s2 : 0, c->walls, c->kp.tiled, c->kp.closure, c->kp.tiled ? c->kp.tile : -1};
+        Key key{c->kp.tiled ? c->kp.s2 : 0, c->walls, c->kp.tiled, c->kp.closure, c->kp.tiled ? c->kp.tile : -1,
+                c->kp.shell_rule};
         auto &g = groups[key];
         if (c->kp.tiled) {
             const int depth = tile_depth(c->kp.tile);
@@ -1175,6 +1206,7 @@ wdlb_status batch_build(wdlb_batch *b)
         G.tiled = g.first.tiled;
         G.closure = g.first.closure;
         G.tile = g.first.tile;
+        G.rule = g.first.rule;
         G.items = b->d_items + all.size();
         G.nitems = (int)g.second.size();
         all.insert(all.end(), g.second.begin(), g.second.end());

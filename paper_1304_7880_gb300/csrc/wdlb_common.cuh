@@ -53,6 +53,8 @@ struct KParams {
     int tile;                // its shape (tile variant 0, 1, 2; see wdlb_shell_tiled.cuh)
     int ball_r;              // largest |component| of a ball vector (halo of the tiled ball sum)
     int ball_tiled;          // 1: use the shared-memory tiled ball sum
+    int shell_rule;          // 0: full shell, uniform weight wshell; 1: compact shell,
+                             // per-vector weights in shell_k[m].w (wshell = 1)
     double g[3];             // external acceleration
     double omega;            // 1/tau
     double tau;
@@ -93,7 +95,7 @@ struct KBufs {
     T *tprev;            // t = sum_e w g2 n(r+e) of the previous step
     T *nscale;           // storage scale of f_in minus n_off, per node
     const int4 *shell_e; // shell vectors
-    const V4<T> *shell_k;// unit vectors e/|e|
+    const V4<T> *shell_k;// unit vectors e/|e| and, in w, the vector's weight (compact shell)
     const int4 *ball;    // ball vectors
     int *status;         // [0]: unstable flag
     double *out_nbar, *out_C, *out_A, *out_u;   // field outputs (fields kernel only)

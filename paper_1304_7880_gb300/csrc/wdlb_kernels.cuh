@@ -514,8 +514,10 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
 // Shell sums of node (x, y, z) with the table in global memory (any sigma,
 // any lattice shape): the (+e, -e) pairs of the library's table, neighbours
 // wrapped periodically in x, y (and z without walls), n = 0 on and beyond the
-// walls.  nu, hb in deviation form (see above).
-template <int CL, bool WALLS, class T>
+// walls.  nu, hb in deviation form (see above).  WT: per-vector quadrature
+// weights (the compact shell) in shell_k[m].w scale the pair's Q; without
+// WT the uniform weight is applied once, in shell_forces.
+template <int CL, bool WALLS, class T, bool WT = false>
 __device__ __forceinline__ void shell_sums_generic(const KParams &p, const V4<T> *nu, const T *hb,
                                                    const int4 *shell_e, const V4<T> *shell_k, int x, int y, int z,
                                                    T hr, T vx, T vy, T vz, ShellAcc<T> &a)
@@ -548,6 +550,11 @@ __device__ __forceinline__ void shell_sums_generic(const KParams &p, const V4<T>
         fetch(-e.x, -e.y, -e.z, nb[1], hbv[1]);
         T qp, qm, qd;
         pair_weights<CL, T>(s0, noff, hbv[0], nb[0].x, hbv[1], nb[1].x, qp, qm, qd);
+        if (WT) {
+            qp *= k.w;
+            qm *= k.w;
+            qd *= k.w;
+        }
         accumulate_pair<T>(a, k.x, k.y, k.z, qp, qm, qd, nb[0].y, nb[0].z, nb[0].w, nb[1].y, nb[1].z, nb[1].w, vx,
                            vy, vz);
     }
@@ -557,7 +564,7 @@ __device__ __forceinline__ void shell_sums_generic(const KParams &p, const V4<T>
 // Fields + collision + streaming, one node per thread, shell table from
 // global memory (any sigma and lattice shape).
 // ---------------------------------------------------------------------------
-template <class S, int CL, bool WALLS, bool FIELDS>
+template <class S, int CL, bool WALLS, bool FIELDS, bool WT = false>
 __device__ __forceinline__ void shell_body(const KParams &p, const KBufs<S, typename Store<S>::T> &b, int blk)
 {
     typedef typename Store<S>::T T;
@@ -581,17 +588,17 @@ __device__ __forceinline__ void shell_body(const KParams &p, const KBufs<S, type
     T tsum = T(0);
     if (p.interactions) {
         ShellAcc<T> a = {};
-        shell_sums_generic<CL, WALLS, T>(p, b.nu, b.hb, b.shell_e, b.shell_k, x, y, z, hr, vx, vy, vz, a);
+        shell_sums_generic<CL, WALLS, T, WT>(p, b.nu, b.hb, b.shell_e, b.shell_k, x, y, z, hr, vx, vy, vz, a);
         shell_forces<T>(p, a, n, vx, vy, vz, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum);
     }
     collide_push<S, CL, WALLS, FIELDS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
                                        [&](int, int dst) { return b.nu[dst].x; });
 }
 
-template <class S, int CL, bool WALLS, bool FIELDS>
+template <class S, int CL, bool WALLS, bool FIELDS, bool WT>
 __global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typename Store<S>::T> b)
 {
-    shell_body<S, CL, WALLS, FIELDS>(p, b, blockIdx.x);
+    shell_body<S, CL, WALLS, FIELDS, WT>(p, b, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------

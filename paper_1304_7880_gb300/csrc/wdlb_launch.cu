@@ -48,46 +48,65 @@ KBufs<S, T> typed(const DevBufs &d, int cur)
 template <int CL, bool WALLS>
 void launch_fields_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st)
 {
-    k_shell_collide<S, CL, WALLS, true><<<blocks_for(p.N), kThreads, 0, st>>>(p, b);
+    if (p.shell_rule)
+        k_shell_collide<S, CL, WALLS, true, true><<<blocks_for(p.N), kThreads, 0, st>>>(p, b);
+    else
+        k_shell_collide<S, CL, WALLS, true, false><<<blocks_for(p.N), kThreads, 0, st>>>(p, b);
 }
 
 #if WDLB_STORAGE != 0
 // The tiled kernel is compiled for the Carnahan-Starling closure (the default),
-// sigma in {3, 4, 6} and the three tile variants; other closures and sigmas
-// use the generic kernel.
-template <int S2, int V, bool WALLS>
+// sigma in {3, 4, 6}, the three tile variants and both shell rules; other
+// closures and sigmas use the generic kernel.
+template <int S2, int V, bool WALLS, bool WT>
 cudaError_t tiled_attr()
 {
-    return cudaFuncSetAttribute(k_step_shell_tiled<S, S2, V, WALLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tiled::smem_bytes<S2, V>());
+    return cudaFuncSetAttribute(k_step_shell_tiled<S, S2, V, WALLS, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tiled::smem_bytes<S2, V, WT>());
 }
 
-template <int S2, int V>
+template <int S2, int V, bool WT>
 cudaError_t tiled_attr_w(bool walls)
 {
-    return walls ? tiled_attr<S2, V, true>() : tiled_attr<S2, V, false>();
+    return walls ? tiled_attr<S2, V, true, WT>() : tiled_attr<S2, V, false, WT>();
+}
+
+template <int S2, bool WT>
+cudaError_t tiled_attr_v(int v, bool walls)
+{
+    return v == 0 ? tiled_attr_w<S2, 0, WT>(walls)
+                  : (v == 1 ? tiled_attr_w<S2, 1, WT>(walls) : tiled_attr_w<S2, 2, WT>(walls));
 }
 
 template <int S2>
-cudaError_t tiled_attr_v(int v, bool walls)
+cudaError_t tiled_attr_r(int v, bool walls, bool wt)
 {
-    return v == 0 ? tiled_attr_w<S2, 0>(walls) : (v == 1 ? tiled_attr_w<S2, 1>(walls) : tiled_attr_w<S2, 2>(walls));
+    return wt ? tiled_attr_v<S2, true>(v, walls) : tiled_attr_v<S2, false>(v, walls);
 }
 
-template <int S2, int V, bool WALLS>
+template <int S2, int V, bool WALLS, bool WT>
 void launch_tiled_group(const BatchLaunch &L, const KBufs<S, float> *B, const BatchGroup &G, cudaStream_t st)
 {
-    k_step_shell_tiled<S, S2, V, WALLS>
-        <<<G.nitems, tiled::threads_of(V), tiled::smem_bytes<S2, V>(), st>>>(L.params, B, G.items);
+    k_step_shell_tiled<S, S2, V, WALLS, WT>
+        <<<G.nitems, tiled::threads_of(V), tiled::smem_bytes<S2, V, WT>(), st>>>(L.params, B, G.items);
+}
+
+template <int S2, int V, bool WT>
+void launch_tiled_r(const BatchLaunch &L, const KBufs<S, float> *B, const BatchGroup &G, cudaStream_t st)
+{
+    if (G.walls)
+        launch_tiled_group<S2, V, true, WT>(L, B, G, st);
+    else
+        launch_tiled_group<S2, V, false, WT>(L, B, G, st);
 }
 
 template <int S2, int V>
 void launch_tiled_w(const BatchLaunch &L, const KBufs<S, float> *B, const BatchGroup &G, cudaStream_t st)
 {
-    if (G.walls)
-        launch_tiled_group<S2, V, true>(L, B, G, st);
+    if (G.rule)
+        launch_tiled_r<S2, V, true>(L, B, G, st);
     else
-        launch_tiled_group<S2, V, false>(L, B, G, st);
+        launch_tiled_r<S2, V, false>(L, B, G, st);
 }
 
 template <int S2>
@@ -116,9 +135,9 @@ bool do_prepare(const KParams &p)
 {
     if (!tiled_eligible(p) || p.tile < 0 || p.tile >= tiled::kVariants) return false;
 #if WDLB_STORAGE != 0
-    const bool walls = p.walls != 0;
-    cudaError_t e = p.s2 == 6 ? tiled_attr_v<6>(p.tile, walls)
-                              : (p.s2 == 8 ? tiled_attr_v<8>(p.tile, walls) : tiled_attr_v<12>(p.tile, walls));
+    const bool walls = p.walls != 0, wt = p.shell_rule != 0;
+    cudaError_t e = p.s2 == 6 ? tiled_attr_r<6>(p.tile, walls, wt)
+                              : (p.s2 == 8 ? tiled_attr_r<8>(p.tile, walls, wt) : tiled_attr_r<12>(p.tile, walls, wt));
     return e == cudaSuccess;
 #else
     return false;
@@ -224,7 +243,13 @@ cudaError_t do_batch_step(const BatchLaunch &L, int parity, int part, int group,
             continue;
         }
 #endif
-#define WDLB_SB(CLV, WV) k_step_shell<S, CLV, WV><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items)
+#define WDLB_SB(CLV, WV)                                                                         \
+    do {                                                                                         \
+        if (G.rule)                                                                              \
+            k_step_shell<S, CLV, WV, true><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items);  \
+        else                                                                                     \
+            k_step_shell<S, CLV, WV, false><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items); \
+    } while (0)
         if (G.closure == 0) { if (G.walls) WDLB_SB(0, true); else WDLB_SB(0, false); }
         else if (G.closure == 1) { if (G.walls) WDLB_SB(1, true); else WDLB_SB(1, false); }
         else { if (G.walls) WDLB_SB(2, true); else WDLB_SB(2, false); }

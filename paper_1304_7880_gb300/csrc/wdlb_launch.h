@@ -40,7 +40,7 @@ struct BatchItem {
 
 // Shell launch of one group of slots with the same kernel variant.
 struct BatchGroup {
-    int s2, walls, tiled, closure, tile;
+    int s2, walls, tiled, closure, tile, rule;   // rule: shell rule (0 full, 1 compact)
     const BatchItem *items;
     int nitems;
 };

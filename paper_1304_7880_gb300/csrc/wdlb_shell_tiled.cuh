@@ -17,7 +17,9 @@
 // (khat_x, khat_y, khat_z, offset of +e in the tile); the loop over them is
 // kept rolled (a few pairs per iteration) so the code stays in the
 // instruction cache.  Each pair goes through pair_weights and accumulate_pair,
-// the same arithmetic as shell_body.
+// the same arithmetic as shell_body.  WT (the compact shell): the pairs are
+// the first nshell/2 of the table, staged with their weights, which scale
+// each pair's Q as in shell_body.
 #pragma once
 
 #include "wdlb_kernels.cuh"
@@ -45,12 +47,13 @@ constexpr int shell_count(int S2)
     return m;
 }
 
-template <int S2, int V>
+template <int S2, int V, bool WT = false>
 constexpr size_t smem_bytes()
 {
     constexpr int R = shell_radius(S2);
     constexpr size_t n = size_t(TX + 2 * R) * (TY + 2 * R) * (tz_of(V) + 2 * R);
-    return n * (sizeof(float4) + sizeof(float)) + size_t(shell_count(S2) / 2) * sizeof(float4);
+    return n * (sizeof(float4) + sizeof(float)) +
+           size_t(shell_count(S2) / 2) * (sizeof(float4) + (WT ? sizeof(float) : 0));
 }
 
 // Blocks per SM the launch bounds ask for: for 256 threads, three where three
@@ -58,16 +61,16 @@ constexpr size_t smem_bytes()
 // registers per thread), else two where two fit, else one; one for 512
 // threads.  Three blocks measured 7-12 % faster than two for sigma 3 (8^3
 // bricks) and sigma 4 (8 x 8 x 4 bricks).
-template <int S2, int V>
+template <int S2, int V, bool WT = false>
 constexpr int blocks_per_sm()
 {
-    return threads_of(V) != 256                            ? 1
-           : 3 * smem_bytes<S2, V>() <= size_t(227) * 1024 ? 3
-           : 2 * smem_bytes<S2, V>() <= size_t(227) * 1024 ? 2
-                                                            : 1;
+    return threads_of(V) != 256                                ? 1
+           : 3 * smem_bytes<S2, V, WT>() <= size_t(227) * 1024 ? 3
+           : 2 * smem_bytes<S2, V, WT>() <= size_t(227) * 1024 ? 2
+                                                                : 1;
 }
 
-template <class S, int S2, int V, int CL, bool WALLS, bool FIELDS>
+template <class S, int S2, int V, int CL, bool WALLS, bool FIELDS, bool WT = false>
 __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, float> &b, int bx, int by, int bz)
 {
     constexpr int R = shell_radius(S2);
@@ -81,15 +84,18 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
     float4 *sm4 = reinterpret_cast<float4 *>(smem_raw);
     float4 *smt = reinterpret_cast<float4 *>(smem_raw + sizeof(float4) * NS);
     float *smh = reinterpret_cast<float *>(smem_raw + sizeof(float4) * (NS + NPAIR));
+    float *smw = smh + NS;                    // pair weights (WT)
+    const int npair = WT ? (p.nshell >> 1) : NPAIR;
 
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
 
     // shell pairs: +e is entry 2m of the library's table (-e is 2m + 1)
-    for (int m = threadIdx.x; m < NPAIR; m += NT) {
+    for (int m = threadIdx.x; m < npair; m += NT) {
         const int4 e = b.shell_e[2 * m];
         const V4<float> k = b.shell_k[2 * m];
         smt[m] = make_float4(k.x, k.y, k.z, __int_as_float(e.x + SX * (e.y + SY * e.z)));
+        if (WT) smw[m] = k.w;
     }
     // the field tile with its halo
     const float noff = float(p.n_off), hoff = float(p.h_off);
@@ -135,8 +141,8 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
             const float s0 = 1.f - hr - hoff;
             // three pairs per iteration; kept rolled for sigma 6 (225 pairs), where
             // it measured 1.5 % faster
-#pragma unroll(S2 >= 12 ? 1 : 3)
-            for (int m = 0; m < NPAIR; m++) {
+#pragma unroll(S2 >= 12 && !WT ? 1 : 3)
+            for (int m = 0; m < npair; m++) {
                 const float4 t = smt[m];
                 const int off = __float_as_int(t.w);
                 const float4 np = sm4[base + off];
@@ -145,6 +151,12 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
                 const float hm = smh[base - off];
                 float qp, qm, qd;
                 pair_weights<CL, float>(s0, noff, hp, np.x, hm, nm.x, qp, qm, qd);
+                if (WT) {
+                    const float r = smw[m];
+                    qp *= r;
+                    qm *= r;
+                    qd *= r;
+                }
                 accumulate_pair<float>(a, t.x, t.y, t.z, qp, qm, qd, np.y, np.z, np.w, nm.y, nm.z, nm.w, me.y,
                                        me.z, me.w);
             }

@@ -48,24 +48,24 @@ __global__ void __launch_bounds__(256) k_step_ball_tiled(const KParams *P, const
     }
 }
 
-template <class S, int CL, bool WALLS>
+template <class S, int CL, bool WALLS, bool WT>
 __global__ void __launch_bounds__(256) k_step_shell(const KParams *P, const KBufs<S, typename Store<S>::T> *B,
                                                     const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
     const KParams p = P[w.slot];
     const KBufs<S, typename Store<S>::T> b = B[w.slot];
-    shell_body<S, CL, WALLS, false>(p, b, w.bx);
+    shell_body<S, CL, WALLS, false, WT>(p, b, w.bx);
 }
 
-template <class S, int S2, int V, bool WALLS>
-__global__ void __launch_bounds__(tiled::threads_of(V), tiled::blocks_per_sm<S2, V>())
+template <class S, int S2, int V, bool WALLS, bool WT>
+__global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2, V, WT>()))
     k_step_shell_tiled(const KParams *P, const KBufs<S, float> *B, const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
     const KParams p = P[w.slot];
     const KBufs<S, float> b = B[w.slot];
-    tiled::tiled_body<S, S2, V, 0, WALLS, false>(p, b, w.bx, w.by, w.bz);
+    tiled::tiled_body<S, S2, V, 0, WALLS, false, WT>(p, b, w.bx, w.by, w.bz);
 }
 
 }  // namespace wdlb

@@ -15,9 +15,11 @@ under the same discrete equations (Sec. 4, Eq. treotto, with the lattice shell
 sums in place of the angular integrals):
     eta / n = kT (tau - 1/2)                                     kinetic
             + (tau - 1/2) K kT n g2 (4 pi sigma^3 / 15)          cross-over (A-term)
-            + (beta / 2) g2 n sum_e w khat_x^2 e_z^2             collisional (F^viscous)
+            + (beta / 2) g2 n sum_e w_e khat_x^2 e_z^2           collisional (F^viscous)
 with beta = 2 sigma^2 sqrt(kT / pi), g2 the Carnahan-Starling contact value at
-the density and w the library's uniform shell weight.
+the density and w_e the weights of the library's contact shell (uniform for
+the full shell; for the compact shell the sum is 4 pi sigma^2 / 15, the
+continuum value).  Every sweep takes the shell rule ("full" or "compact").
 """
 from __future__ import annotations
 
@@ -37,30 +39,32 @@ def contact_value(chi: float) -> float:
     return (1.0 - 0.5 * chi) / (1.0 - chi) ** 3
 
 
-def bulk_shear_viscosity(n: float, sigma: float, tau: float, k_cross: float = 2.0) -> float:
+def bulk_shear_viscosity(n: float, sigma: float, tau: float, k_cross: float = 2.0,
+                         shell_rule: str = "full") -> float:
     """Dynamic shear viscosity of the uniform fluid of density n (long-wave limit
     of the discrete equations), in lattice units."""
-    e, wshell = w.wdlb_stencil(sigma, 1)
+    e, wshell = w.wdlb_shell_table(sigma, shell_rule)
     e = e.astype(np.float64)
     khat = e / np.linalg.norm(e, axis=1)[:, None]
     g2 = contact_value(math.pi * sigma ** 3 * n / 6.0)
     beta = 2.0 * sigma ** 2 * math.sqrt(KT / math.pi)
     kinetic = KT * (tau - 0.5)
     cross = (tau - 0.5) * k_cross * KT * n * g2 * (4.0 * math.pi * sigma ** 3 / 15.0)
-    collisional = 0.5 * beta * g2 * n * wshell * float(np.sum(khat[:, 0] ** 2 * e[:, 2] ** 2))
+    collisional = 0.5 * beta * g2 * n * float(np.sum(wshell * khat[:, 0] ** 2 * e[:, 2] ** 2))
     return n * (kinetic + cross + collisional)
 
 
 def pore_viscosity_sweep(chi: float, widths, sigma: float = 4.0, tau: float = 1.0, gx: float = 1e-6,
                          nxy: int = 8, tol: float = 1e-8, max_steps: int = 2_000_000, storage: str = "f32",
-                         budget_bytes: int = 8 << 30, timeout_s: float = 1800.0):
+                         budget_bytes: int = 8 << 30, timeout_s: float = 1800.0, shell_rule: str = "full"):
     """Steady slit Poiseuille flow at packing fraction chi for every hydrodynamic
     width H in `widths` (lattice units; nz = H + 2), uniform initial density,
     cross-section nxy x nxy (the state stays uniform in x and y).  Returns one
     dict per width with H, steps, mean density, eta_eff, eta_bulk and their
     ratio, in the order of `widths`."""
     n0 = synth.packing_to_density(chi, sigma)
-    srv = w.wdlb_server_create(budget_bytes, max_active=max(1, len(widths)), check_every=100, storage=storage)
+    srv = w.wdlb_server_create(budget_bytes, max_active=max(1, len(widths)), check_every=100, storage=storage,
+                               shell_rule=shell_rule)
     ids = {}
     try:
         for H in widths:
@@ -85,7 +89,7 @@ def pore_viscosity_sweep(chi: float, widths, sigma: float = 4.0, tau: float = 1.
             out.append({"H": int(H), "status": None if r is None else r["status"]})
             continue
         st = r["stats"]
-        eta_b = bulk_shear_viscosity(st["mean_n"], sigma, tau)
+        eta_b = bulk_shear_viscosity(st["mean_n"], sigma, tau, shell_rule=shell_rule)
         out.append({"H": int(H), "status": 0, "steps": r["steps"], "mean_n": st["mean_n"],
                     "eta_eff": st["eta_eff"], "eta_bulk": eta_b, "ratio": st["eta_eff"] / eta_b,
                     "seconds": r["finish_s"] - r["start_s"]})
@@ -93,7 +97,7 @@ def pore_viscosity_sweep(chi: float, widths, sigma: float = 4.0, tau: float = 1.
 
 
 def bulk_viscosity_sweep(chis, sigma: float = 8.0, tau: float = 1.0, k_values=(2.0, 0.0), L: int = 256,
-                         nxy: int = 8, amplitude: float = 1e-6, storage: str = "f32"):
+                         nxy: int = 8, amplitude: float = 1e-6, storage: str = "f32", shell_rule: str = "full"):
     """Bulk shear viscosity against packing fraction (Sec. 5, the experiment
     behind Fig. 1): a uniform fluid at rest is perturbed by a transverse wave
     u_x = a sin(2 pi z / L) on an nxy x nxy x L periodic box, and its decay
@@ -109,7 +113,7 @@ def bulk_viscosity_sweep(chis, sigma: float = 8.0, tau: float = 1.0, k_values=(2
     for chi in chis:
         n0 = synth.packing_to_density(chi, sigma)
         for K in k_values:
-            eta_th = bulk_shear_viscosity(n0, sigma, tau, K)
+            eta_th = bulk_shear_viscosity(n0, sigma, tau, K, shell_rule)
             rate_th = eta_th / n0 * q * q
             span = int(math.ceil(1.0 / rate_th))               # one e-fold
             every = max(1, span // 8)
@@ -117,7 +121,7 @@ def bulk_viscosity_sweep(chis, sigma: float = 8.0, tau: float = 1.0, k_values=(2
             u = np.zeros((3, L, nxy, nxy))
             u[0] = amplitude * sz[:, None, None]
             ctx = w.wdlb_create((nxy, nxy, L), sigma, False, tau, (0.0, 0.0, 0.0), storage=storage,
-                                k_cross=K)
+                                k_cross=K, shell_rule=shell_rule)
             w.wdlb_init_fields(ctx, n, u)
             w.wdlb_step(ctx, span // 10)
             t, a = [], []

@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_UNST
 CLOSURES = {"CS": 0, "PY": 1, "ONE": 2}
 OMEGA_MODES = {"const": 0, "nbar": 1}
 STORAGES = {"f64": 0, "f32": 1, "f16": 2}
+SHELL_RULES = {"full": 0, "compact": 1}
 
 
 class WDLBError(RuntimeError):
@@ -41,7 +42,8 @@ class wdlb_options(ctypes.Structure):
     _fields_ = [("closure", ctypes.c_int32), ("omega_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("interactions", ctypes.c_int32), ("k_cross", ctypes.c_double), ("n_ref", ctypes.c_double),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("tile", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("shell_rule", ctypes.c_int32)]
 
 
 class wdlb_pore_desc(ctypes.Structure):
@@ -96,6 +98,7 @@ def load_library(path: str = LIB_PATH):
         "wdlb_autotune_reset": (None, []),
         "wdlb_velocity_set": (I32, [P, P]),
         "wdlb_stencil": (I32, [D, I32, P, I32, P, P]),
+        "wdlb_shell_table": (I32, [D, I32, P, P, I32, P]),
         "wdlb_profile_step": (I32, [P, I64, P]),
         "wdlb_fields_static": (I32, [wdlb_lattice, D, I32, I32, P, P, P, P, P, P]),
         "wdlb_launch_count": (I64, [P]),
@@ -163,9 +166,11 @@ class Context:
 
 
 def wdlb_create(lattice, sigma, walls, tau, g=(0.0, 0.0, 0.0), closure="CS", omega_mode="const",
-                storage="f32", interactions=True, k_cross=2.0, n_ref=0.0, device=None, tile=-1, autotune=True):
+                storage="f32", interactions=True, k_cross=2.0, n_ref=0.0, device=None, tile=-1, autotune=True,
+                shell_rule="full"):
     """Create a context; device memory and stream come from PyTorch.  tile: -1
-    (autotuner) or a forced tile shape 0, 1, 2 of the tiled shell kernel."""
+    (autotuner) or a forced tile shape 0, 1, 2 of the tiled shell kernel;
+    shell_rule: "full" or "compact" contact-shell quadrature."""
     import torch
 
     lib = load_library()
@@ -181,6 +186,7 @@ def wdlb_create(lattice, sigma, walls, tau, g=(0.0, 0.0, 0.0), closure="CS", ome
     opt.n_ref = float(n_ref)
     opt.tile = int(tile)
     opt.autotune = 1 if autotune else 0
+    opt.shell_rule = SHELL_RULES[shell_rule]
     walls_i = 1 if walls else 0
     nbytes = ctypes.c_uint64()
     _check(lib.wdlb_workspace_size(lat, float(sigma), walls_i, ctypes.byref(opt), ctypes.byref(nbytes)))
@@ -273,15 +279,17 @@ def wdlb_load_state(ctx: Context, buf: np.ndarray):
     _check(load_library().wdlb_load_state(ctx.handle, _ptr(buf), ctypes.c_uint64(buf.nbytes)), ctx)
 
 
-def wdlb_autotune(lattice, sigma, walls, storage="f32", device=None):
-    """Time the tiled shell kernel's shapes for this (storage, sigma, walls, nz)
-    now and record the fastest; returns (best, [ms per step of shapes 0, 1, 2])."""
+def wdlb_autotune(lattice, sigma, walls, storage="f32", device=None, shell_rule="full"):
+    """Time the tiled shell kernel's shapes for this (storage, sigma, walls, nz,
+    shell rule) now and record the fastest; returns (best, [ms per step of
+    shapes 0, 1, 2])."""
     import torch
 
     lib = load_library()
     opt = wdlb_options()
     lib.wdlb_default_options(ctypes.byref(opt))
     opt.storage = STORAGES[storage]
+    opt.shell_rule = SHELL_RULES[shell_rule]
     nx, ny, nz = (int(v) for v in lattice)
     best = ctypes.c_int32()
     ms = (ctypes.c_double * 3)()
@@ -331,6 +339,18 @@ def wdlb_stencil(sigma: float, which: int):
     v = np.zeros((cnt.value, 3), dtype=np.int32)
     _check(lib.wdlb_stencil(float(sigma), int(which), _ptr(v), cnt.value, ctypes.byref(cnt), ctypes.byref(w)))
     return v, w.value
+
+
+def wdlb_shell_table(sigma: float, rule: str = "full"):
+    """Contact shell of a quadrature rule: vectors (m, 3), +e and -e adjacent,
+    and the weight of each (m,)."""
+    lib = load_library()
+    cnt = ctypes.c_int32()
+    _check(lib.wdlb_shell_table(float(sigma), SHELL_RULES[rule], None, None, 0, ctypes.byref(cnt)))
+    v = np.zeros((cnt.value, 3), dtype=np.int32)
+    w = np.zeros(cnt.value)
+    _check(lib.wdlb_shell_table(float(sigma), SHELL_RULES[rule], _ptr(v), _ptr(w), cnt.value, ctypes.byref(cnt)))
+    return v, w
 
 
 def wdlb_profile_step(ctx: Context, nsteps: int):
@@ -403,7 +423,7 @@ def _bcheck(status, batch=None):
 
 
 def wdlb_batch_create(max_pores, pool_bytes, closure="CS", omega_mode="const", storage="f32", interactions=True,
-                      k_cross=2.0, device=None):
+                      k_cross=2.0, device=None, shell_rule="full"):
     import torch
 
     lib = load_library()
@@ -414,6 +434,7 @@ def wdlb_batch_create(max_pores, pool_bytes, closure="CS", omega_mode="const", s
     opt.storage = STORAGES[storage]
     opt.interactions = 1 if interactions else 0
     opt.k_cross = float(k_cross)
+    opt.shell_rule = SHELL_RULES[shell_rule]
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     pool = torch.empty(int(pool_bytes) + 256, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -512,7 +533,8 @@ class Server:
             wdlb_server_destroy(self)
 
 
-def wdlb_server_create(hbm_budget, max_active=256, check_every=100, closure="CS", storage="f32", device=None):
+def wdlb_server_create(hbm_budget, max_active=256, check_every=100, closure="CS", storage="f32", device=None,
+                       shell_rule="full"):
     """Serving loop (native worker thread) over a batch whose pool is a torch tensor."""
     import torch
 
@@ -521,6 +543,7 @@ def wdlb_server_create(hbm_budget, max_active=256, check_every=100, closure="CS"
     lib.wdlb_default_options(ctypes.byref(opt))
     opt.closure = CLOSURES[closure]
     opt.storage = STORAGES[storage]
+    opt.shell_rule = SHELL_RULES[shell_rule]
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     pool = torch.empty(int(hbm_budget) + 256, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)

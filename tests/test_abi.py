@@ -58,6 +58,41 @@ def test_stencils_match_oracle(lib, oracle_mod, sigma):
     assert (e[0::2] == -e[1::2]).all()
 
 
+def test_compact_shell_matches_oracle(lib, oracle_mod):
+    """The compact quadrature (two or three cubic orbits, weights from three
+    moment conditions) is rebuilt independently on both sides: the same vectors
+    at every sigma on a 0.05 grid, weights within the two solvers' rounding,
+    and no shell where the oracle has none."""
+    worst = 0.0
+    for sigma in np.round(np.arange(1.0, 8.0001, 0.05), 2):
+        ref = oracle_mod.shell_compact(float(sigma))
+        if ref is None:
+            with pytest.raises(lib.WDLBError):
+                lib.wdlb_shell_table(float(sigma), "compact")
+            continue
+        e, w = lib.wdlb_shell_table(float(sigma), "compact")
+        got = {tuple(v): x for v, x in zip(e.tolist(), w)}
+        exp = {tuple(v): x for v, x in zip(ref[0].tolist(), ref[1])}
+        assert got.keys() == exp.keys(), sigma
+        worst = max(worst, max(abs(got[k] / exp[k] - 1) for k in got))
+        assert (e[0::2] == -e[1::2]).all()
+    assert worst < 1e-9
+    e, w = lib.wdlb_shell_table(4.0, "full")
+    assert len(e) == 210 and np.all(w == lib.wdlb_stencil(4.0, 1)[1])
+
+
+def test_compact_rule_refused_where_it_has_no_shell(lib):
+    so = lib.load_library()
+    opt = lib.wdlb_options()
+    so.wdlb_default_options(ctypes.byref(opt))
+    opt.shell_rule = 1
+    nb = ctypes.c_uint64()
+    assert so.wdlb_workspace_size(lib.wdlb_lattice(8, 8, 8), 1.5, 0, ctypes.byref(opt), ctypes.byref(nb)) == 1
+    assert so.wdlb_workspace_size(lib.wdlb_lattice(8, 8, 8), 4.0, 0, ctypes.byref(opt), ctypes.byref(nb)) == 0
+    opt.shell_rule = 2
+    assert so.wdlb_workspace_size(lib.wdlb_lattice(8, 8, 8), 4.0, 0, ctypes.byref(opt), ctypes.byref(nb)) == 1
+
+
 def test_invalid_arguments_rejected(lib):
     so = lib.load_library()
     lat = lib.wdlb_lattice(8, 8, 41)
