@@ -13,6 +13,9 @@
 // v_z) and hb - h_off, R = floor(sigma + 1/2), with periodic wrap in x, y (and
 // z without walls) and n = 0 beyond the walls, so the shell loop needs no
 // bounds checks: a solid or missing neighbour has n = 0 and adds nothing.
+// The tile arrives by cp.async (16 bytes of nu, 4 of hb per node), so all
+// of a thread's halo loads are in flight together (measured 3 % faster for
+// the full sigma-4 shell, 8 to 18 % for the compact shells).
 // The (+e, -e) pairs of the contact shell are staged once per block as
 // (khat_x, khat_y, khat_z, offset of +e in the tile); the loop over them is
 // kept rolled (a few pairs per iteration) so the code stays in the
@@ -109,17 +112,18 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
             inside = gz >= 0 && gz < nz;
         else
             gz = wrap_coord(gz, nz);
-        float4 v = make_float4(-noff, 0.f, 0.f, 0.f);   // beyond a wall: n = 0
-        float h = -hoff;
-        if (inside) {
+        if (inside) {   // asynchronous copies: every load of the tile is in flight at once
             const int g = gx + nx * (gy + ny * gz);
-            const V4<float> t = b.nu[g];
-            v = make_float4(t.x, t.y, t.z, t.w);
-            h = b.hb[g];
+            const unsigned d4 = (unsigned)__cvta_generic_to_shared(sm4 + idx);
+            const unsigned dh = (unsigned)__cvta_generic_to_shared(smh + idx);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d4), "l"(b.nu + g) : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dh), "l"(b.hb + g) : "memory");
+        } else {        // beyond a wall: n = 0
+            sm4[idx] = make_float4(-noff, 0.f, 0.f, 0.f);
+            smh[idx] = -hoff;
         }
-        sm4[idx] = v;
-        smh[idx] = h;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
 
     const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tzb = threadIdx.x >> 6;
