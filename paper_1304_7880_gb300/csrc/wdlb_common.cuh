@@ -101,6 +101,17 @@ struct KBufs {
     double *out_nbar, *out_C, *out_A, *out_u;   // field outputs (fields kernel only)
 };
 
+// Asynchronous global -> shared copy of BYTES (4, 8 or 16) bytes, both
+// addresses aligned to BYTES; cp_async_wait_all waits for all of the thread's
+// copies (a __syncthreads must follow before other threads read them).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_ca(void *smem, const void *gmem)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Contact value of the homogeneous hard-sphere pair distribution at packing
 // fraction chi (closure 0: Carnahan-Starling, 1: Percus-Yevick, 2: one).
 template <int CL, class T>

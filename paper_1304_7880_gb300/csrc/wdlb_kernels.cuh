@@ -189,7 +189,8 @@ __device__ __forceinline__ void ball_body(const KParams &p, const V4<T> *nu, T *
 // Tiled form of ball_body: one 8 x 8 x 8 brick of nodes per block of 256
 // threads (two nodes per thread, z and z + 4), with n - n_off of the brick
 // and its halo of ball_r, and the ball's offsets within it, in shared memory.
-// Beyond a wall the staged value is -n_off (n = 0).  The ball points are
+// Beyond a wall the staged value is -n_off (n = 0).  The brick arrives by
+// cp.async (all of a thread's loads in flight at once).  The ball points are
 // added in table order, so every sum is bitwise the one of ball_body.
 template <class T>
 __device__ __forceinline__ void ball_tiled_body(const KParams &p, const V4<T> *nu, T *hb, const int4 *ball,
@@ -214,8 +215,12 @@ __device__ __forceinline__ void ball_tiled_body(const KParams &p, const V4<T> *n
             inside = gz >= 0 && gz < p.nz;
         else
             gz = wrap_coord(gz, p.nz);
-        sn[idx] = inside ? nu[gx + p.nx * (gy + p.ny * gz)].x : -noff;
+        if (inside)
+            cp_async_ca<sizeof(T)>(sn + idx, &nu[gx + p.nx * (gy + p.ny * gz)].x);
+        else
+            sn[idx] = -noff;
     }
+    cp_async_wait_all();
     __syncthreads();
     const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tzb = threadIdx.x >> 6;
     for (int half = 0; half < 2; half++) {
@@ -236,7 +241,7 @@ __device__ __forceinline__ void ball_tiled_body(const KParams &p, const V4<T> *n
     }
 }
 
-// ball_tiled_body with 2 sigma = S2 known at compile time (sigma 3, 4, 6): the
+// ball_tiled_body with 2 sigma = S2 known at compile time (sigma 3, 4, 6, 8): the
 // brick side and the ball's offsets are constants, and the points are added
 // in the order of the host's ball table (dx, then dy, then dz ascending), so
 // the sums are bitwise those of ball_body and ball_tiled_body.
@@ -259,8 +264,12 @@ __device__ __forceinline__ void ball_brick_ct(const KParams &p, const V4<T> *nu,
             inside = gz >= 0 && gz < p.nz;
         else
             gz = wrap_coord(gz, p.nz);
-        sn[idx] = inside ? nu[gx + p.nx * (gy + p.ny * gz)].x : -noff;
+        if (inside)
+            cp_async_ca<sizeof(T)>(sn + idx, &nu[gx + p.nx * (gy + p.ny * gz)].x);
+        else
+            sn[idx] = -noff;
     }
+    cp_async_wait_all();
     __syncthreads();
     const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tzb = threadIdx.x >> 6;
     for (int half = 0; half < 2; half++) {

@@ -114,16 +114,14 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
             gz = wrap_coord(gz, nz);
         if (inside) {   // asynchronous copies: every load of the tile is in flight at once
             const int g = gx + nx * (gy + ny * gz);
-            const unsigned d4 = (unsigned)__cvta_generic_to_shared(sm4 + idx);
-            const unsigned dh = (unsigned)__cvta_generic_to_shared(smh + idx);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d4), "l"(b.nu + g) : "memory");
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dh), "l"(b.hb + g) : "memory");
+            cp_async_ca<16>(sm4 + idx, b.nu + g);
+            cp_async_ca<4>(smh + idx, b.hb + g);
         } else {        // beyond a wall: n = 0
             sm4[idx] = make_float4(-noff, 0.f, 0.f, 0.f);
             smh[idx] = -hoff;
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    cp_async_wait_all();
     __syncthreads();
 
     const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tzb = threadIdx.x >> 6;

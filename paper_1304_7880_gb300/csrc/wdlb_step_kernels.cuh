@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256) k_step_ball_tiled(const KParams *P, const
     case 6: ball_brick_ct<T, 6>(p, b.nu, b.hb, b.status, w.bx, w.by, w.bz); break;
     case 8: ball_brick_ct<T, 8>(p, b.nu, b.hb, b.status, w.bx, w.by, w.bz); break;
     case 12: ball_brick_ct<T, 12>(p, b.nu, b.hb, b.status, w.bx, w.by, w.bz); break;
+    case 16: ball_brick_ct<T, 16>(p, b.nu, b.hb, b.status, w.bx, w.by, w.bz); break;
     default: ball_tiled_body<T>(p, b.nu, b.hb, b.ball, b.status, w.bx, w.by, w.bz); break;
     }
 }
