@@ -497,8 +497,10 @@ def run_ours(args):
                                                             for r in bres if r["K"] == 2.0],
                                 "seconds": time.perf_counter() - t0}
         t0 = time.perf_counter()
-        cres = sweeps.bulk_viscosity_sweep([0.05, 0.1, 0.15, 0.2, 0.25, 0.3, 0.35], shell_rule="compact")
+        # the compact shell's density limit at sigma 8 lies between n* = 0.5 and 0.55 (chi 0.26-0.29)
+        cres = sweeps.bulk_viscosity_sweep([0.05, 0.1, 0.15, 0.2, 0.25], shell_rule="compact")
         sweep["bulk_sigma8_compact_shell"] = {
+            "chi": [r["chi"] for r in cres if r["K"] == 2.0],
             "eta_K2": [r["eta"] for r in cres if r["K"] == 2.0],
             "eta_K0": [r["eta"] for r in cres if r["K"] == 0.0],
             "measured_over_theory_K2": [round(r["eta"] / r["eta_theory"], 5) for r in cres if r["K"] == 2.0],
