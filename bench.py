@@ -484,6 +484,11 @@ def run_ours(args):
             res = sweeps.pore_viscosity_sweep(chi, widths)
             sweep["ratio_chi_%g" % chi] = [round(r["ratio"], 5) if r["status"] == 0 else None for r in res]
         dt = time.perf_counter() - t0
+        # the compact contact shell on the dilute pore (chi 0.32 is above its density limit)
+        t1 = time.perf_counter()
+        cres_p = sweeps.pore_viscosity_sweep(0.11, widths, shell_rule="compact")
+        sweep["ratio_chi_0.11_compact_shell"] = [round(r["ratio"], 5) if r["status"] == 0 else None for r in cres_p]
+        sweep["compact_shell_seconds"] = time.perf_counter() - t1
         sweep["solves"] = 2 * len(widths)
         sweep["seconds"] = dt
         sweep["solves_per_s"] = 2 * len(widths) / dt

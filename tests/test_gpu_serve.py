@@ -66,6 +66,37 @@ def test_server_results_equal_alone(w):
         assert r["finish_s"] >= r["start_s"] >= r["submit_s"]
 
 
+def test_server_compact_shell_results_equal_alone(w):
+    """A server on the compact contact shell: sigma 3, 4 and 6 requests in one
+    batch, each equal bit for bit to the request solved alone with that rule."""
+    reqs = [REQUESTS[0], REQUESTS[2], REQUESTS[5]]
+    srv = w.wdlb_server_create(64 << 20, max_active=4, check_every=100, shell_rule="compact")
+    ids = {}
+    for k, (lat, sigma, nstar, gx, seed) in enumerate(reqs):
+        p, n, u = synth.slit_poiseuille(*lat, nstar, sigma, 1.0, gx, seed)
+        ids[w.wdlb_server_submit(srv, lat, sigma, True, 1.0, p["g"], n, u, tol=TOL, max_steps=200000,
+                                 want_moments=True)] = k
+    results = {}
+    t0 = time.time()
+    while len(results) < len(ids) and time.time() - t0 < 300:
+        for r in w.wdlb_server_poll(srv):
+            results[ids[r["id"]]] = r
+        time.sleep(0.01)
+    w.wdlb_server_destroy(srv)
+    assert len(results) == len(reqs)
+    for k, (lat, sigma, nstar, gx, seed) in enumerate(reqs):
+        r = results[k]
+        assert r["status"] == 0 and r["residual"] < TOL
+        p, n, u = synth.slit_poiseuille(*lat, nstar, sigma, 1.0, gx, seed)
+        ctx = w.wdlb_create(lat, sigma, True, 1.0, p["g"], storage="f32", shell_rule="compact")
+        w.wdlb_init_fields(ctx, n, u)
+        steps, _ = w.wdlb_run_steady(ctx, TOL, 100, 200000)
+        n_a, u_a = w.wdlb_moments(ctx)
+        w.wdlb_destroy(ctx)
+        assert r["steps"] == steps
+        assert np.array_equal(r["n"], n_a) and np.array_equal(r["u"], u_a)
+
+
 def test_server_rejects_a_pore_larger_than_its_budget(w):
     srv = w.wdlb_server_create(4 << 20, max_active=2, check_every=100)
     p, n, u = synth.slit_poiseuille(32, 32, 65, 0.3, 4.0, 1.0, 1e-6, 7)
