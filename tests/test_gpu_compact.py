@@ -221,3 +221,25 @@ def test_compact_bulk_viscosity_sweep_is_the_continuum_value(w):
                     + beta * g2 * n * 2 * math.pi * sigma ** 2 / 15)
         assert r["eta_theory"] == pytest.approx(cont, rel=1e-12)
         assert r["eta"] == pytest.approx(cont, rel=5e-3)
+
+
+@pytest.mark.parametrize("case", ["s3.5_f64", "s3.5_f32", "s2_f64", "py_closure_f64"])
+def test_compact_generic_kernel_edge_cases(w, oracle_mod, case):
+    """The generic shell kernel with per-vector weights where the tiled kernel
+    does not apply: sigma 3.5 (no compiled tile), sigma 2 (the smallest sigma
+    with a compact rule, 38 vectors), the Percus-Yevick closure."""
+    sigma = {"s3.5_f64": 3.5, "s3.5_f32": 3.5, "s2_f64": 2.0, "py_closure_f64": 4.0}[case]
+    storage = "f32" if case.endswith("f32") else "f64"
+    closure = "PY" if case.startswith("py") else "CS"
+    p = dict(nx=11, ny=9, nz=15, walls=True, sigma=sigma, tau=0.9, g=(1e-5, 0, 0))
+    n, u = noisy_state(p, 0.4, 2e-2, 29)
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    ctx = w.wdlb_create((nx, ny, nz), sigma, True, p["tau"], p["g"], storage=storage, closure=closure,
+                        shell_rule="compact")
+    w.wdlb_init_fields(ctx, n, u)
+    assert w.wdlb_tile_info(ctx)[0] is False
+    o = oracle_mod.Oracle(nx, ny, nz, True, sigma, p["tau"], p["g"], closure=closure, shell_rule="compact")
+    o.init(n, u)
+    w.wdlb_step(ctx, 15)
+    o.step(15)
+    compare(ctx, o, True, TOL[storage], w)
