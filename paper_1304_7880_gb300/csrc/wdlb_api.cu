@@ -17,9 +17,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/wdlb.h"
 #include "wdlb_launch.h"
 #include "wdlb_tables.h"
+
+namespace {
+// NVTX range over a host-side phase of the library (named in Nsight Systems
+// timelines and selectable with ncu --nvtx); NVTX is header-only and costs a
+// null check when no tool is attached.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+}  // namespace
 
 using namespace wdlb;
 
@@ -185,6 +199,8 @@ wdlb_status check_status_word(wdlb_ctx *ctx)
     int h = 0;
     WDLB_CUDA(ctx, cudaMemcpyAsync(&h, ctx->dev.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     WDLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h & kStatusBounds)
+        return fail(ctx, WDLB_ERR_CUDA, "checked build: a kernel index left its array (the access was skipped)");
     if (h) return fail(ctx, WDLB_ERR_UNSTABLE, "non-physical state: smeared packing fraction >= 1 or density not finite/positive");
     return WDLB_OK;
 }
@@ -433,6 +449,7 @@ int tile_builtin(int s2, int walls, int nz)
 wdlb_status probe_tiles(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_options &o, int *best,
                         double ms[3])
 {
+    TraceRange tr("autotune_probe");
     int side = (int)std::ceil(std::sqrt(double(1 << 20) / double(lat.nz)) / 8.0) * 8;
     side = std::max(8, std::min(side, 512));
     wdlb_lattice pl{side, side, lat.nz};
@@ -639,6 +656,7 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
 
 wdlb_status wdlb_init_fields(wdlb_ctx *ctx, const double *n, const double *u)
 {
+    TraceRange tr("wdlb_init_fields");
     if (!ctx || !n) return ctx ? fail(ctx, WDLB_ERR_ARG, "n is NULL") : WDLB_ERR_ARG;
     double *sn = ctx->dev.stage, *su = ctx->dev.stage + ctx->N;
     WDLB_CUDA(ctx, cudaMemcpyAsync(sn, n, ctx->N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
@@ -657,6 +675,7 @@ wdlb_status wdlb_init_fields_device(wdlb_ctx *ctx, const double *d_n, const doub
 
 wdlb_status wdlb_step(wdlb_ctx *ctx, int64_t nsteps)
 {
+    TraceRange tr("wdlb_step");
     if (!ctx) return WDLB_ERR_ARG;
     if (nsteps < 0) return fail(ctx, WDLB_ERR_ARG, "nsteps < 0");
     if (!ctx->initialised) return fail(ctx, WDLB_ERR_STATE, "wdlb_step before wdlb_init_fields");
@@ -688,6 +707,7 @@ wdlb_status wdlb_moments_device(wdlb_ctx *ctx, double *d_n, double *d_u)
 
 wdlb_status wdlb_moments(wdlb_ctx *ctx, double *n, double *u)
 {
+    TraceRange tr("wdlb_moments");
     if (!ctx) return WDLB_ERR_ARG;
     double *sn = ctx->dev.stage, *su = ctx->dev.stage + ctx->N;
     wdlb_status s = wdlb_moments_device(ctx, sn, su);
@@ -778,6 +798,7 @@ static double flux_residual(wdlb_ctx *ctx, const double r[6], int64_t interval)
 wdlb_status wdlb_run_steady(wdlb_ctx *ctx, double tol, int32_t check_every, int64_t max_steps,
                             int64_t *steps_done, double *residual)
 {
+    TraceRange tr("wdlb_run_steady");
     if (!ctx) return WDLB_ERR_ARG;
     if (check_every < 1 || max_steps < 0 || !(tol > 0)) return fail(ctx, WDLB_ERR_ARG, "bad steady-state arguments");
     if (!ctx->initialised) return fail(ctx, WDLB_ERR_STATE, "run_steady before init");
@@ -1126,6 +1147,7 @@ void batch_drop_graph(wdlb_batch *b)
 // Rebuild the device tables after slots changed.
 wdlb_status batch_build(wdlb_batch *b)
 {
+    TraceRange tr("batch_build");
     const int P = (int)b->slots.size();
     std::vector<KParams> params(P);
     std::vector<char> bufs0(b->L->kbufs_bytes * P, 0), bufs1(b->L->kbufs_bytes * P, 0);
@@ -1414,6 +1436,7 @@ wdlb_status wdlb_batch_remove(wdlb_batch *b, int32_t slot)
 
 wdlb_status wdlb_batch_step(wdlb_batch *b, int64_t nsteps)
 {
+    TraceRange tr("wdlb_batch_step");
     if (!b || nsteps < 0) return WDLB_ERR_ARG;
     if (b->dirty) {
         wdlb_status s = batch_build(b);
@@ -1472,7 +1495,8 @@ wdlb_status wdlb_batch_residuals(wdlb_batch *b, int32_t interval, double *res, i
             c->last_residual = v;
         }
         if (res) res[s] = v;
-        if (status) status[s] = c ? (stw[s] ? WDLB_ERR_UNSTABLE : WDLB_OK) : -1;
+        if (status)
+            status[s] = c ? ((stw[s] & kStatusBounds) ? WDLB_ERR_CUDA : (stw[s] ? WDLB_ERR_UNSTABLE : WDLB_OK)) : -1;
     }
     return WDLB_OK;
 }
@@ -1607,64 +1631,68 @@ void server_loop(wdlb_server *s)
     for (;;) {
         // admit while there is room
         bool admitted_now = false;
-        for (;;) {
-            wdlb_server::Pending p;
-            {
-                std::unique_lock<std::mutex> lock(s->mu);
-                if (s->stop) return;
-                if (s->queue.empty()) {
-                    if (wdlb_batch_active(s->batch) == 0) {
-                        s->cv.wait_for(lock, std::chrono::milliseconds(2));
-                        continue;
+        {
+            TraceRange tr_admit("server_admit");
+            for (;;) {
+                wdlb_server::Pending p;
+                {
+                    std::unique_lock<std::mutex> lock(s->mu);
+                    if (s->stop) return;
+                    if (s->queue.empty()) {
+                        if (wdlb_batch_active(s->batch) == 0) {
+                            s->cv.wait_for(lock, std::chrono::milliseconds(2));
+                            continue;
+                        }
+                        break;
                     }
-                    break;
-                }
-                uint64_t need = 0;
-                if (wdlb_batch_pore_bytes(s->batch, &s->queue.front().req.desc, &need) != WDLB_OK) need = 0;
-                if (need == 0 || need > wdlb_batch_free_bytes(s->batch)) {
-                    if (wdlb_batch_active(s->batch) == 0 && need != 0) {
-                        // larger than the whole pool: reject it
-                        p = std::move(s->queue.front());
-                        s->queue.pop_front();
-                        lock.unlock();
-                        wdlb_result r;
-                        std::memset(&r, 0, sizeof(r));
-                        r.id = p.id;
-                        r.status = WDLB_ERR_OOM;
-                        r.submit_s = r.start_s = p.submit_s;
-                        r.finish_s = server_now(s);
-                        std::lock_guard<std::mutex> l2(s->mu);
-                        s->done.push_back(r);
-                        s->completed++;
-                        continue;
+                    uint64_t need = 0;
+                    if (wdlb_batch_pore_bytes(s->batch, &s->queue.front().req.desc, &need) != WDLB_OK) need = 0;
+                    if (need == 0 || need > wdlb_batch_free_bytes(s->batch)) {
+                        if (wdlb_batch_active(s->batch) == 0 && need != 0) {
+                            // larger than the whole pool: reject it
+                            p = std::move(s->queue.front());
+                            s->queue.pop_front();
+                            lock.unlock();
+                            wdlb_result r;
+                            std::memset(&r, 0, sizeof(r));
+                            r.id = p.id;
+                            r.status = WDLB_ERR_OOM;
+                            r.submit_s = r.start_s = p.submit_s;
+                            r.finish_s = server_now(s);
+                            std::lock_guard<std::mutex> l2(s->mu);
+                            s->done.push_back(r);
+                            s->completed++;
+                            continue;
+                        }
+                        break;
                     }
-                    break;
+                    p = std::move(s->queue.front());
+                    s->queue.pop_front();
                 }
-                p = std::move(s->queue.front());
-                s->queue.pop_front();
-            }
-            int32_t slot = -1;
-            wdlb_status a = wdlb_batch_add(s->batch, &p.req.desc, p.n.data(), p.u.empty() ? nullptr : p.u.data(), &slot);
-            if (a != WDLB_OK) {
-                std::lock_guard<std::mutex> lock(s->mu);
-                if (a == WDLB_ERR_OOM) {   // fragmentation or slots: retry later
-                    s->queue.push_front(std::move(p));
-                    break;
+                int32_t slot = -1;
+                wdlb_status a = wdlb_batch_add(s->batch, &p.req.desc, p.n.data(),
+                                               p.u.empty() ? nullptr : p.u.data(), &slot);
+                if (a != WDLB_OK) {
+                    std::lock_guard<std::mutex> lock(s->mu);
+                    if (a == WDLB_ERR_OOM) {   // fragmentation or slots: retry later
+                        s->queue.push_front(std::move(p));
+                        break;
+                    }
+                    wdlb_result r;
+                    std::memset(&r, 0, sizeof(r));
+                    r.id = p.id;
+                    r.status = a;
+                    r.submit_s = r.start_s = p.submit_s;
+                    r.finish_s = server_now(s);
+                    s->done.push_back(r);
+                    s->completed++;
+                    continue;
                 }
-                wdlb_result r;
-                std::memset(&r, 0, sizeof(r));
-                r.id = p.id;
-                r.status = a;
-                r.submit_s = r.start_s = p.submit_s;
-                r.finish_s = server_now(s);
-                s->done.push_back(r);
-                s->completed++;
-                continue;
+                s->active[slot] = wdlb_server::Active{p.id, p.req, p.submit_s, server_now(s)};
+                s->active[slot].req.n = s->active[slot].req.u = nullptr;
+                s->admitted++;
+                admitted_now = true;
             }
-            s->active[slot] = wdlb_server::Active{p.id, p.req, p.submit_s, server_now(s)};
-            s->active[slot].req.n = s->active[slot].req.u = nullptr;
-            s->admitted++;
-            admitted_now = true;
         }
         // u_x snapshot of the new pores (the others' snapshots are re-taken at the same state)
         if (admitted_now) wdlb_batch_residuals(s->batch, s->check_every, res.data(), st.data());

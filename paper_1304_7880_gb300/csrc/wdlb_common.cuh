@@ -101,6 +101,31 @@ struct KBufs {
     double *out_nbar, *out_C, *out_A, *out_u;   // field outputs (fields kernel only)
 };
 
+// Checked build (compile with -DWDLB_CHECKED=1): every index the step
+// kernels compute into a global or shared array is tested against the array's
+// extent.  An index outside it sets bit 2 of the status word and the access is
+// skipped, so a wrong index is reported instead of reading or writing another
+// buffer.  In the normal build the test is the constant true.
+#ifndef WDLB_CHECKED
+#define WDLB_CHECKED 0
+#endif
+constexpr int kStatusUnstable = 1;   // status word bits
+constexpr int kStatusBounds = 2;
+
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int *status)
+{
+#if WDLB_CHECKED
+    if (i >= 0 && i < n) return true;
+    atomicOr(status, kStatusBounds);
+    return false;
+#else
+    (void)i;
+    (void)n;
+    (void)status;
+    return true;
+#endif
+}
+
 // Asynchronous global -> shared copy of BYTES (4, 8 or 16) bytes, both
 // addresses aligned to BYTES; cp_async_wait_all waits for all of the thread's
 // copies (a __syncthreads must follow before other threads read them).

@@ -179,7 +179,8 @@ __device__ __forceinline__ void ball_body(const KParams &p, const V4<T> *nu, T *
         }
         int xx = wrap_coord(x + e.x, p.nx);
         int yy = wrap_coord(y + e.y, p.ny);
-        sum += nu[xx + p.nx * (yy + p.ny * zz)].x;
+        const int j = xx + p.nx * (yy + p.ny * zz);
+        if (in_bounds(j, p.N, status)) sum += nu[j].x;
     }
     T dh = T(p.c_half) * sum;
     if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
@@ -215,8 +216,9 @@ __device__ __forceinline__ void ball_tiled_body(const KParams &p, const V4<T> *n
             inside = gz >= 0 && gz < p.nz;
         else
             gz = wrap_coord(gz, p.nz);
-        if (inside)
-            cp_async_ca<sizeof(T)>(sn + idx, &nu[gx + p.nx * (gy + p.ny * gz)].x);
+        const int g = gx + p.nx * (gy + p.ny * gz);
+        if (inside && in_bounds(g, p.N, status))
+            cp_async_ca<sizeof(T)>(sn + idx, &nu[g].x);
         else
             sn[idx] = -noff;
     }
@@ -234,7 +236,8 @@ __device__ __forceinline__ void ball_tiled_body(const KParams &p, const V4<T> *n
         }
         const int base = (tx + R) + SX * ((ty + R) + SX * (tz + R));
         T sum = T(0);
-        for (int m = 0; m < p.nball; m++) sum += sn[base + so[m]];
+        for (int m = 0; m < p.nball; m++)
+            if (in_bounds(base + so[m], NS, status)) sum += sn[base + so[m]];
         T dh = T(p.c_half) * sum;
         if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
         hb[i] = dh;
@@ -264,8 +267,9 @@ __device__ __forceinline__ void ball_brick_ct(const KParams &p, const V4<T> *nu,
             inside = gz >= 0 && gz < p.nz;
         else
             gz = wrap_coord(gz, p.nz);
-        if (inside)
-            cp_async_ca<sizeof(T)>(sn + idx, &nu[gx + p.nx * (gy + p.ny * gz)].x);
+        const int g = gx + p.nx * (gy + p.ny * gz);
+        if (inside && in_bounds(g, p.N, status))
+            cp_async_ca<sizeof(T)>(sn + idx, &nu[g].x);
         else
             sn[idx] = -noff;
     }
@@ -289,7 +293,9 @@ __device__ __forceinline__ void ball_brick_ct(const KParams &p, const V4<T> *nu,
             for (int dy = -R; dy <= R; dy++)
 #pragma unroll
                 for (int dz = -R; dz <= R; dz++)
-                    if (16 * (dx * dx + dy * dy + dz * dz) <= S2 * S2) sum += c[dx + SX * (dy + SX * dz)];
+                    if (16 * (dx * dx + dy * dy + dz * dz) <= S2 * S2 &&
+                        in_bounds(c - sn + dx + SX * (dy + SX * dz), NS, status))
+                        sum += c[dx + SX * (dy + SX * dz)];
         T dh = T(p.c_half) * sum;
         if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
         hb[i] = dh;
@@ -510,6 +516,7 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
             dst = xt + nx * (yt + ny * zt);
             dn_t = q == 0 ? dn_self : target_dn(q, dst);
         }
+        if (!in_bounds(dst, p.N, b.status)) continue;
         const T stored = post + wq * (dsc - dn_t);
         Store<S>::put(b.f_out + (size_t)qq * p.Npad + dst, stored, T(1.0 / w_of(q)) * fast_rcp<T>(noff + dn_t));
     }
@@ -529,7 +536,7 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
 template <int CL, bool WALLS, class T, bool WT = false>
 __device__ __forceinline__ void shell_sums_generic(const KParams &p, const V4<T> *nu, const T *hb,
                                                    const int4 *shell_e, const V4<T> *shell_k, int x, int y, int z,
-                                                   T hr, T vx, T vy, T vz, ShellAcc<T> &a)
+                                                   T hr, T vx, T vy, T vz, ShellAcc<T> &a, int *status)
 {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const T noff = T(p.n_off), hoff = T(p.h_off);
@@ -541,11 +548,11 @@ __device__ __forceinline__ void shell_sums_generic(const KParams &p, const V4<T>
             solid = zz <= 0 || zz >= nz - 1;
         else
             zz = wrap_coord(zz, nz);
-        if (solid) {
+        const int j = solid ? 0 : wrap_coord(x + ex, nx) + nx * (wrap_coord(y + ey, ny) + ny * zz);
+        if (solid || !in_bounds(j, p.N, status)) {
             nb = V4<T>{-noff, T(0), T(0), T(0)};
             hbv = -hoff;
         } else {
-            const int j = wrap_coord(x + ex, nx) + nx * (wrap_coord(y + ey, ny) + ny * zz);
             nb = nu[j];
             hbv = hb[j];
         }
@@ -597,11 +604,14 @@ __device__ __forceinline__ void shell_body(const KParams &p, const KBufs<S, type
     T tsum = T(0);
     if (p.interactions) {
         ShellAcc<T> a = {};
-        shell_sums_generic<CL, WALLS, T, WT>(p, b.nu, b.hb, b.shell_e, b.shell_k, x, y, z, hr, vx, vy, vz, a);
+        shell_sums_generic<CL, WALLS, T, WT>(p, b.nu, b.hb, b.shell_e, b.shell_k, x, y, z, hr, vx, vy, vz, a,
+                                             b.status);
         shell_forces<T>(p, a, n, vx, vy, vz, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum);
     }
     collide_push<S, CL, WALLS, FIELDS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
-                                       [&](int, int dst) { return b.nu[dst].x; });
+                                       [&](int, int dst) {
+                                           return in_bounds(dst, p.N, b.status) ? b.nu[dst].x : T(0);
+                                       });
 }
 
 template <class S, int CL, bool WALLS, bool FIELDS, bool WT>

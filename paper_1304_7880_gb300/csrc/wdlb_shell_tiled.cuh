@@ -112,8 +112,8 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
             inside = gz >= 0 && gz < nz;
         else
             gz = wrap_coord(gz, nz);
-        if (inside) {   // asynchronous copies: every load of the tile is in flight at once
-            const int g = gx + nx * (gy + ny * gz);
+        const int g = gx + nx * (gy + ny * gz);
+        if (inside && in_bounds(g, p.N, b.status)) {   // asynchronous copies: all loads in flight at once
             cp_async_ca<16>(sm4 + idx, b.nu + g);
             cp_async_ca<4>(smh + idx, b.hb + g);
         } else {        // beyond a wall: n = 0
@@ -147,6 +147,7 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
             for (int m = 0; m < npair; m++) {
                 const float4 t = smt[m];
                 const int off = __float_as_int(t.w);
+                if (!in_bounds(base + off, NS, b.status) || !in_bounds(base - off, NS, b.status)) continue;
                 const float4 np = sm4[base + off];
                 const float hp = smh[base + off];
                 const float4 nm = sm4[base - off];
@@ -167,7 +168,10 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
         }
         collide_push<S, CL, WALLS, FIELDS>(
             p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
-            [&](int q, int) { return sm4[base + cx_of(q) + SX * (cy_of(q) + SY * cz_of(q))].x; });
+            [&](int q, int) {
+                const int k = base + cx_of(q) + SX * (cy_of(q) + SY * cz_of(q));
+                return in_bounds(k, NS, b.status) ? sm4[k].x : 0.f;
+            });
     }
 }
 

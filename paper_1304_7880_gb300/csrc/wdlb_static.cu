@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(256) k_static_fields(KParams p0, StaticBufs s,
     const float hr = float(p.h_off) + s.hb[i];
     const V4<float> me = s.nu[i];
     ShellAcc<float> a = {};
-    shell_sums_generic<CL, WALLS, float>(p, s.nu, s.hb, s.shell_e, s.shell_k, x, y, z, hr, me.y, me.z, me.w, a);
+    shell_sums_generic<CL, WALLS, float>(p, s.nu, s.hb, s.shell_e, s.shell_k, x, y, z, hr, me.y, me.z, me.w, a,
+                                         s.status);
     float C[3], A[6], t;
     shell_forces<float>(p, a, float(p.n_off) + me.x, me.y, me.z, me.w, C[0], C[1], C[2], A[0], A[1], A[2], A[3], A[4],
                         A[5], t);

@@ -11,12 +11,14 @@ Arrays: node index i = x + nx*(y + ny*z), numpy shape (nz, ny, nx); vectors
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libwdlb.so")
+# WDLB_LIBRARY selects another build of the library (the bounds-checked one).
+LIB_PATH = os.environ.get("WDLB_LIBRARY") or os.path.join(_HERE, "_build", "libwdlb.so")
 _lib = None
 
 WDLB_OK = 0
@@ -527,6 +529,7 @@ class Server:
         self.pool = pool
         self.stream = stream
         self.keep = {}     # id -> host arrays that must outlive the request
+        self.nodes = {}    # id -> lattice nodes (for the per-solve log)
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -582,11 +585,15 @@ def wdlb_server_submit(server, lattice, sigma, walls, tau, g, n, u=None, tol=1e-
     if st != WDLB_OK:
         raise WDLBError(st, "wdlb_server_submit")
     server.keep[rid.value] = outs
+    server.nodes[rid.value] = nx * ny * nz
     return rid.value
 
 
-def wdlb_server_poll(server, cap=1024):
-    """Finished results: list of dicts (with 'n', 'u' if moments were requested)."""
+def wdlb_server_poll(server, cap=1024, log=None):
+    """Finished results: list of dicts (with 'n', 'u' if moments were
+    requested).  log: a writable text file that receives one JSON line per
+    finished solve (id, status, steps, residual, queue, run and total seconds,
+    nodes, MLUPS of the solve, mean density, flux, effective viscosity)."""
     buf = (wdlb_result * cap)()
     k = load_library().wdlb_server_poll(server.handle, buf, cap)
     out = []
@@ -597,7 +604,18 @@ def wdlb_server_poll(server, cap=1024):
         outs = server.keep.pop(r.id, None)
         if outs is not None:
             d["n"], d["u"] = outs
+        nodes = server.nodes.pop(r.id, 0)
+        if log is not None:
+            run_s = r.finish_s - r.start_s
+            rec = {"id": r.id, "status": STATUS_NAMES.get(r.status, r.status), "steps": r.steps,
+                   "residual": r.residual, "queue_s": r.start_s - r.submit_s, "run_s": run_s,
+                   "latency_s": r.finish_s - r.submit_s, "nodes": nodes,
+                   "mlups": nodes * r.steps / run_s / 1e6 if run_s > 0 else None,
+                   "mean_n": r.stats.mean_n, "flux_x": r.stats.flux_x, "eta_eff": r.stats.eta_eff}
+            log.write(json.dumps(rec) + "\n")
         out.append(d)
+    if log is not None:
+        log.flush()
     return out
 
 

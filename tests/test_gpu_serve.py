@@ -2,6 +2,8 @@
 others are being stepped are admitted into the running batch, and each
 result equals the same request solved alone with wdlb_run_steady (same
 kernels, same residual cadence), also while sharing the device with a mix."""
+import io
+import json
 import time
 
 import numpy as np
@@ -77,13 +79,17 @@ def test_server_compact_shell_results_equal_alone(w):
         ids[w.wdlb_server_submit(srv, lat, sigma, True, 1.0, p["g"], n, u, tol=TOL, max_steps=200000,
                                  want_moments=True)] = k
     results = {}
+    log = io.StringIO()              # one JSON line per finished solve
     t0 = time.time()
     while len(results) < len(ids) and time.time() - t0 < 300:
-        for r in w.wdlb_server_poll(srv):
+        for r in w.wdlb_server_poll(srv, log=log):
             results[ids[r["id"]]] = r
         time.sleep(0.01)
     w.wdlb_server_destroy(srv)
     assert len(results) == len(reqs)
+    recs = [json.loads(line) for line in log.getvalue().splitlines()]
+    assert sorted(r["id"] for r in recs) == sorted(ids)
+    assert all(r["status"] == "OK" and r["mlups"] > 0 and r["latency_s"] >= r["run_s"] for r in recs)
     for k, (lat, sigma, nstar, gx, seed) in enumerate(reqs):
         r = results[k]
         assert r["status"] == 0 and r["residual"] < TOL
