@@ -46,7 +46,10 @@ typedef enum {
     WDLB_OK = 0,
     WDLB_ERR_ARG = 1,      /* invalid argument; nothing was changed             */
     WDLB_ERR_OOM = 2,      /* device allocation failed or workspace too small   */
-    WDLB_ERR_CUDA = 3,     /* a CUDA call failed; message in wdlb_last_error    */
+    WDLB_ERR_CUDA = 3,     /* a CUDA call failed; message in wdlb_last_error.
+                              Also: in the bounds-checked build
+                              (libwdlb_checked.so), a kernel index outside its
+                              array (the access was skipped)                    */
     WDLB_ERR_UNSTABLE = 4, /* smeared packing fraction >= 1 or non-finite state */
     WDLB_ERR_TIMEOUT = 5,  /* a bounded wait ran out, or a served request hit its
                               step cap before its steady-state tolerance        */
@@ -306,7 +309,8 @@ wdlb_status wdlb_batch_step(wdlb_batch *b, int64_t nsteps);
 /* Per slot (array of max_pores): the FP64 steady-state residual of
  * wdlb_run_steady, |Q - Q(previous call)| / (interval |Q|) with Q the pore flux
  * (+inf at a pore's first call, NaN for empty slots), and the slot status
- * (WDLB_OK, WDLB_ERR_UNSTABLE, -1 empty); either array may be NULL.
+ * (WDLB_OK, WDLB_ERR_UNSTABLE, WDLB_ERR_CUDA for the checked build's index
+ * flag, -1 empty); either array may be NULL.
  * Synchronous. */
 wdlb_status wdlb_batch_residuals(wdlb_batch *b, int32_t interval, double *res, int32_t *status);
 /* The context of a slot (owned by the batch): use it for wdlb_moments,
