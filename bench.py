@@ -358,7 +358,7 @@ def run_ours(args):
     barrier()
     from paper_1304_7880_gb300 import wdlb as w
 
-    p, n_h, u_h = synth.bulk_shear_128(seed=2 + rank)
+    p, n_h, u_h = synth.bulk_shear_128(seed=2 + rank, sigma=SIGMA)
     N = L ** 3
     shape = (p["nx"], p["ny"], p["nz"])
 
@@ -581,11 +581,11 @@ def run_ours(args):
     step_ms = sum(kms)
     hbm_achieved = BYTES_PER_NODE["f32"] * N / (step_ms * 1e-3) / 1e9
     wt = "true" if args.shell_rule == "compact" else "false"
-    kname = (("k_step_shell_tiled<float, 8, %d, false, %s>" % (tile_info[1], wt)) if tile_info[0]
+    kname = (("k_step_shell_tiled<float, %d, %d, false, %s>" % (int(round(2 * SIGMA)), tile_info[1], wt)) if tile_info[0]
              else "k_step_shell<float, 0, false, %s>" % wt)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tflops, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak,
-                "traffic": recorded_traffic() if args.shell_rule == "full" else None,
+                "traffic": recorded_traffic() if args.shell_rule == "full" and SIGMA == 4.0 else None,
                 "peak_source": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts)",
                 "flops_per_node": flops_per_node,
                 "share_of_step": shell_ms / step_ms if step_ms > 0 else None,
@@ -624,7 +624,7 @@ def run_ours(args):
 
 
 def main():
-    global SUB
+    global SUB, SIGMA, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -632,6 +632,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--sigma", type=float, default=SIGMA,
+                    help="hard-sphere diameter of the main box (lattice units); the workload is quoted at 4")
     ap.add_argument("--shell-rule", default="full", choices=["full", "compact"],
                     help="contact-shell quadrature of the main timed workload")
     ap.add_argument("--only-device", action="store_true",
@@ -643,6 +645,9 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     SUB = args.sub
+    if args.sigma != SIGMA:
+        SIGMA = args.sigma
+        WORKLOAD = WORKLOAD.replace("sigma=4 lattice units", "sigma=%g lattice units" % SIGMA)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -74,9 +74,9 @@ def slit_8x8x41(seed: int = 1):
     return params, n, u
 
 
-def bulk_shear_128(seed: int = 2, L: int = 128):
-    """Bulk periodic box L^3, sigma=4, packing fraction 0.3, shear wave 1e-4, noise 1e-4."""
-    sigma = 4.0
+def bulk_shear_128(seed: int = 2, L: int = 128, sigma: float = 4.0):
+    """Bulk periodic box L^3, sigma (default 4), packing fraction 0.3, shear wave 1e-4, noise 1e-4."""
+    sigma = float(sigma)
     n0 = packing_to_density(0.3, sigma)
     n, u = shear_wave(L, L, L, n0, 1e-4, 1e-4, seed)
     params = dict(nx=L, ny=L, nz=L, walls=False, sigma=sigma, tau=1.0, g=(0.0, 0.0, 0.0))
