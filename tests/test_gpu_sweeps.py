@@ -113,3 +113,17 @@ def test_bulk_viscosity_point_matches_oracle(sweeps, oracle_mod):
         a.append(2.0 / L * float(np.sum(o.moments()[1][0, :, 0, 0] * sz)))
     eta_oracle = n0 * (-np.polyfit(t, np.log(a), 1)[0]) / (q * q)
     assert gpu["eta"] == pytest.approx(eta_oracle, rel=1e-3)
+
+
+def test_compact_shell_pore_viscosity_against_the_full_shell(sweeps):
+    """The compact contact shell in confinement (chi = 0.11, sigma 4): it lowers
+    the effective viscosity of a narrow slit (the wall layers are
+    finite-wavenumber structure, where the two quadratures differ) and meets the
+    full shell's value in a wide one (both tend to their common long-wave bulk
+    viscosity)."""
+    full = sweeps.pore_viscosity_sweep(0.11, [8, 200])
+    comp = sweeps.pore_viscosity_sweep(0.11, [8, 200], shell_rule="compact")
+    assert all(r["status"] == 0 for r in full + comp)
+    assert comp[0]["ratio"] < full[0]["ratio"] < comp[1]["ratio"]
+    assert comp[1]["ratio"] == pytest.approx(full[1]["ratio"], rel=0.01)
+    assert comp[1]["ratio"] > 0.95
