@@ -161,3 +161,27 @@ def test_a_failing_pore_is_flagged_alone(w):
     f_b = w.wdlb_get_populations(w.wdlb_batch_context(b, good))
     assert np.array_equal(f_b, alone(w, PORES[0], 10))
     w.wdlb_batch_destroy(b)
+
+
+def test_batch_slot_checkpoint_resumes_alone(w):
+    """A pore checkpointed inside a batch resumes in a context of its own and
+    continues bit for bit as it does in the batch (checkpoint of a slot context;
+    same kernels alone and batched)."""
+    lat, sigma, walls, tau, g, nstar, seed = PORES[0]
+    b = w.wdlb_batch_create(4, 64 << 20, storage="f32")
+    slots = []
+    for k in (0, 2):
+        lt, sg, wl, ta, gg, ns, sd = PORES[k]
+        n, u = pore_fields(lt, sg, wl, ns, sd)
+        slots.append(w.wdlb_batch_add(b, lt, sg, wl, ta, gg, n, u))
+    w.wdlb_batch_step(b, 9)
+    blob = w.wdlb_save_state(w.wdlb_batch_context(b, slots[0]))
+    n, u = pore_fields(lat, sigma, walls, nstar, seed)
+    ctx = w.wdlb_create(lat, sigma, walls, tau, g, storage="f32")
+    w.wdlb_init_fields(ctx, n, u)
+    w.wdlb_load_state(ctx, blob)
+    w.wdlb_step(ctx, 6)
+    w.wdlb_batch_step(b, 6)
+    assert np.array_equal(w.wdlb_get_populations(ctx), w.wdlb_get_populations(w.wdlb_batch_context(b, slots[0])))
+    w.wdlb_destroy(ctx)
+    w.wdlb_batch_destroy(b)
