@@ -1,18 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the WDLB lattice update on GB300.
 
-Workload: bulk periodic box 128^3, sigma = 4 lattice units, packing fraction
-0.3, FP32 deviation storage with FP64 reductions, transverse shear wave
-u_x = 1e-4 sin(2 pi z / 128) on a uniform density with seeded 1e-4 relative
-noise.  One benchmark step = 100 lattice time steps (each: moments and field
-velocity, smeared density, shell sums + collision + streaming) followed by the
-FP64 pore-average reduction.  Metric: MLUPS (lattice-node updates per second).
+Headline workload: 64 slit pores in one batch (widths H uniform in [3 sigma,
+30 sigma] at sigma = 4, i.e. 13-121 z-nodes, x-y 32 x 32, n* uniform in
+[0.1, 0.6], g_x log-uniform in [1e-7, 1e-5], tau = 1), FP32 deviation storage
+with FP64 reductions.  One benchmark step = 100 lattice time steps of every
+pore (each: moments and field velocity, smeared density, shell sums +
+collision + streaming; one launch per phase for all pores, replayed from a
+CUDA graph) followed by the FP64 steady-state residual of every pore.  Metric:
+MLUPS (lattice-node updates per second).  Further legs: the 128^3 bulk box
+(FP32, FP16, FP64, compact shell), the 256 x 256 x 161 slit, serving, the
+viscosity sweeps, and the FP64 oracle on the host cores.
 
   python bench.py [--gpus N --steps K --warmup W]      this library (C ABI)
   python bench.py --impl reference ...                 the FP64 CPU oracle
 
 With N > 1 (torchrun, one rank per GPU) every rank runs its own replica of the
-box (the workload has no exchange step): weak scaling, no collective on the
+batch (the workload has no exchange step): weak scaling, no collective on the
 data path; the elapsed time is the maximum over ranks.
 """
 from __future__ import annotations
@@ -35,11 +39,15 @@ if ROOT not in sys.path:
 METRIC = "MLUPS (lattice-node updates/s) & HBM roofline frac, batched FP32 vs plain FP64; p50/p99 solve"
 UNIT = "MLUPS"
 L = 128
-SIGMA = 4.0
+SIGMA = 4.0                    # sigma of the 128^3 box legs (--sigma)
+BATCH_SIGMA = 4.0              # sigma of the batched pores
 SUB = 100                      # lattice time steps per benchmark step
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
+BATCH_WORKLOAD = ("64 slit pores 32x32x(13..121) (H uniform in [3 sigma, 30 sigma]), sigma=4 lattice units, "
+                  "walls z=0 and z=nz-1, n* uniform in [0.1, 0.6] (the scheme's stability limit in slits), "
+                  "g_x log-uniform in [1e-7, 1e-5], tau=1, D3Q19, Carnahan-Starling contact value, K=2, "
+                  "seeded 1e-3 density noise")
 WORKLOAD = ("bulk periodic box 128^3, sigma=4 lattice units, packing fraction 0.3, D3Q19, "
             "Carnahan-Starling contact value, K=2, tau=1, shear wave u_x=1e-4 sin(2 pi z/128), 1e-4 density noise")
 
@@ -141,13 +149,13 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_shell_tiled_bulk128_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_shell_tiled_batch64_traffic.txt")
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the shell kernel from the committed ncu summary
-    (lines "key: value"), used only if it was taken on the current kernel
-    sources and the same lattice."""
+def recorded_traffic(nodes):
+    """DRAM bytes per launch of the batch's shell kernel from the committed ncu
+    summary (lines "key: value"), used only if it was taken on the current
+    kernel sources and a workload of the same node count."""
     try:
         rec = {}
         with open(TRAFFIC_FILE) as fh:
@@ -155,7 +163,7 @@ def recorded_traffic():
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     rec[k.strip()] = v.strip()
-        if rec.get("source_hash") == kernel_source_hash() and int(rec.get("nodes", -1)) == L ** 3:
+        if rec.get("source_hash") == kernel_source_hash() and int(rec.get("nodes", -1)) == nodes:
             return float(rec["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -198,21 +206,110 @@ def dist_env():
     return world, rank, local
 
 
-def cpu_baseline_oracle(timesteps=1, box=L):
-    """The FP64 oracle on the host, as it stands (single thread)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(conn, pore_index, count, seed):
+    """One host process stepping one pore of the batched workload with the
+    oracle, on command ("step", k) -> replies the nodes updated."""
     import oracle
     from paper_1304_7880_gb300 import synth
-    oracle.build()
-    p, n, u = synth.bulk_shear_128(L=box)
-    o = oracle.Oracle(p["nx"], p["ny"], p["nz"], p["walls"], p["sigma"], p["tau"], p["g"])
+    pp, n, u = synth.batched_pores(count=count, seed=seed)[pore_index]
+    o = oracle.Oracle(pp["nx"], pp["ny"], pp["nz"], pp["walls"], pp["sigma"], pp["tau"], pp["g"])
     o.init(n, u)
+    nodes = pp["nx"] * pp["ny"] * pp["nz"]
+    conn.send(("ready", nodes))
+    while True:
+        msg = conn.recv()
+        if msg[0] == "stop":
+            break
+        o.step(int(msg[1]))
+        conn.send(("done", nodes * int(msg[1])))
+    conn.close()
+
+
+class OraclePool:
+    """`procs` host processes (started with spawn, never forked from a process
+    that holds a CUDA context), each holding one pore of the batched workload
+    in the oracle.  step(k) runs k time steps of every pore concurrently and
+    returns the lattice-node updates done."""
+
+    def __init__(self, procs, count=64, seed=4):
+        import multiprocessing as mp
+        import oracle
+        oracle.build()                 # once, before the workers load it
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for k in range(procs):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, k % count, count, seed), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        self.nodes = [c.recv()[1] for c in self.conns]
+
+    def step(self, k):
+        for c in self.conns:
+            c.send(("step", k))
+        return sum(c.recv()[1] for c in self.conns)
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_oracle():
+    """The FP64 oracle as it stands, on bounded samples of the batched
+    workload: one pore on one host thread, then one pore per host core
+    stepped concurrently (independent processes)."""
+    model = cpu_model()
+    one = OraclePool(1)
     t0 = time.perf_counter()
-    o.step(timesteps)
-    dt = time.perf_counter() - t0
-    nodes = box ** 3
-    return {"value": nodes * timesteps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d time step(s) of the %d^3 box (same sigma, density and initial fields), %.1f s"
-                      % (timesteps, box, dt)}
+    done = one.step(2)
+    dt1 = time.perf_counter() - t0
+    one.close()
+    cores = host_cores()
+    pool = OraclePool(cores)
+    pool.step(1)                       # warm-up
+    t0 = time.perf_counter()
+    done_all = pool.step(2)
+    dt_all = time.perf_counter() - t0
+    pool.close()
+    return {"value": done_all / dt_all / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_model": model,
+            "sample": "2 time steps of %d pores of the 64-pore batch, one pore per host core in its own process "
+                      "(%d nodes, %.1f s)" % (cores, sum(pool.nodes), dt_all),
+            "single_thread": {"value": done / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": "2 time steps of pore 0 of the batch (%d nodes, %.1f s)" % (done // 2, dt1)}}
 
 
 def run_serving(w, synth, np, rate, window_s, drain_s, max_active=48, tol=1e-8):
@@ -246,11 +343,21 @@ def run_serving(w, synth, np, rate, window_s, drain_s, max_active=48, tol=1e-8):
     info = w.wdlb_server_info(srv)
     w.wdlb_server_destroy(srv)
     ok = [r for r in done if r["status"] == 0]
+    by_status = {}
+    for r in done:
+        name = w.STATUS_NAMES.get(r["status"], str(r["status"]))
+        by_status[name] = by_status.get(name, 0) + 1
+    failed = [{"id": r["id"], "status": w.STATUS_NAMES.get(r["status"], str(r["status"])), "steps": r["steps"],
+               "residual": r["residual"], "sigma": submitted[r["id"]]["sigma"],
+               "H": submitted[r["id"]]["nz"] - 2, "nxy": submitted[r["id"]]["nx"],
+               "n_star": round(submitted[r["id"]]["n_star"], 4), "g_x": submitted[r["id"]]["gx"]}
+              for r in done if r["status"] != 0]
     lat = np.array([r["finish_s"] - r["submit_s"] for r in ok]) if ok else np.array([np.nan])
     node_steps = sum(submitted[r["id"]]["nx"] * submitted[r["id"]]["ny"] * submitted[r["id"]]["nz"] * r["steps"]
                      for r in ok)
     return {"offered_rate_per_s": round(rate, 3), "arrival_window_s": window_s, "submitted": len(submitted),
-            "completed": len(ok), "failed": len(done) - len(ok), "elapsed_s": round(elapsed, 3),
+            "completed": len(ok), "failed": len(done) - len(ok), "by_status": by_status, "failed_requests": failed,
+            "elapsed_s": round(elapsed, 3),
             "solves_per_s": len(ok) / elapsed, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "backlog_at_end": info["queued"] + info["active"],
             "completed_mlups": node_steps / elapsed / 1e6, "server_mlups": info["node_steps"] / elapsed / 1e6,
@@ -306,35 +413,42 @@ def run_serving_pair(w, synth, np):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host's cores, one
+    pore of the batched workload per core in its own process; one benchmark
+    step = one time step of every such pore."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    box = 32
-    per_step = 4
-    cfg = {"workload": WORKLOAD, "sample": "%d^3 box, %d time steps per benchmark step" % (box, per_step),
-           "nodes": box ** 3, "parallelism": "single host thread"}
-    import oracle
-    from paper_1304_7880_gb300 import synth
-    oracle.build()
-    p, n, u = synth.bulk_shear_128(L=box)
-    o = oracle.Oracle(p["nx"], p["ny"], p["nz"], p["walls"], p["sigma"], p["tau"], p["g"])
-    o.init(n, u)
+    cores = host_cores()
+    pool = OraclePool(cores)
     for _ in range(args.warmup):
-        o.step(per_step)
+        pool.step(1)
+    done = 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o.step(per_step)
+        done += pool.step(1)
     dt = time.perf_counter() - t0
-    value = box ** 3 * per_step * args.steps / dt / 1e6
+    nodes = sum(pool.nodes)
+    pool.close()
+    value = done / dt / 1e6
+    sample = ("1 time step per benchmark step of %d of the batch's 64 pores (%d nodes), one pore per host core, "
+              "each in its own process" % (cores, nodes))
+    cfg = {"workload": BATCH_WORKLOAD, "sample": sample, "nodes": nodes,
+           "parallelism": "%d host processes (%s)" % (cores, cpu_model())}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": cfg["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def fp32_peak_tflops(sm_count, sm_mhz):
+    """FP32 FMA issue peak: SMs x 128 lanes x 2 flops x clock."""
+    return sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
 def run_ours(args):
@@ -358,6 +472,113 @@ def run_ours(args):
     barrier()
     from paper_1304_7880_gb300 import wdlb as w
 
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+    alu_peak = fp32_peak_tflops(sm_count, SM_MAX_MHZ_NOMINAL)
+    peaks, peak_kind = measured_peaks()
+
+    # ---------------- headline: the 64-pore batch, device-resident ----------------
+    pores = synth.batched_pores(seed=4 + rank, sigma=BATCH_SIGMA)
+    nodes_b = sum(pp["nx"] * pp["ny"] * pp["nz"] for pp, _, _ in pores)
+    probe = w.wdlb_batch_create(1, 1 << 20, storage="f32")
+    pool = 0
+    for pp, _, _ in pores:
+        pool += (w.wdlb_batch_pore_bytes(probe, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"]) + 255) // 256 * 256
+    w.wdlb_batch_destroy(probe)
+    bt = w.wdlb_batch_create(len(pores), pool + (1 << 20), storage="f32")
+    slots = [w.wdlb_batch_add(bt, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"], pp["tau"], pp["g"], nn, uu)
+             for pp, nn, uu in pores]
+    tiles = sorted({w.wdlb_tile_info(w.wdlb_batch_context(bt, s)) for s in slots})
+
+    def batch_bench_step():
+        w.wdlb_batch_step(bt, SUB)
+        return w.wdlb_batch_residuals(bt, SUB)
+
+    for _ in range(args.warmup):
+        batch_bench_step()
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    launches0 = w.wdlb_batch_launch_count(bt)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(bt.stream)
+    for _ in range(args.steps):
+        batch_bench_step()
+    ev1.record(bt.stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if rank == 0 else None
+    gpu_launches = w.wdlb_batch_launch_count(bt) - launches0
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    value = job_mlups(world, nodes_b, SUB * args.steps, elapsed_ms * 1e-3)
+    res, st = w.wdlb_batch_residuals(bt, SUB)
+    assert all(int(st[s]) == 0 for s in slots), st
+    # per-kernel durations for the roofline: the same batch stepped phase by
+    # phase with CUDA events around each launch on the batch stream
+    prof_steps = max(1, min(args.steps, 5))
+    kms = [0.0, 0.0, 0.0]
+    torch.cuda.synchronize()
+    ia = torch.cuda.Event(enable_timing=True)
+    ib = torch.cuda.Event(enable_timing=True)
+    ia.record(bt.stream)
+    for _ in range(prof_steps):
+        ms = w.wdlb_batch_profile_step(bt, SUB)
+        for k in range(3):
+            kms[k] += ms[k] / prof_steps
+    ib.record(bt.stream)
+    torch.cuda.synchronize()
+    instrumented_ms = max_over_ranks(ia.elapsed_time(ib)) / prof_steps
+    w.wdlb_batch_destroy(bt)
+
+    if args.only_device:
+        if rank == 0:
+            print(json.dumps({"only_device": True, "value": value, "unit": UNIT, "ms_per_step": elapsed_ms / args.steps,
+                              "time_steps_per_step": SUB, "kernels_ms": kms, "instrumented_ms_per_step": instrumented_ms,
+                              "gpu_launches": int(gpu_launches), "tiles": tiles}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---------------- end to end through the public batch API and host buffers ----------------
+    pin = []
+    for pp, nn, uu in pores:
+        a = torch.empty(nn.shape, dtype=torch.float64, pin_memory=True)
+        b = torch.empty(uu.shape, dtype=torch.float64, pin_memory=True)
+        a.copy_(torch.from_numpy(nn))
+        b.copy_(torch.from_numpy(uu))
+        on = torch.empty(nn.shape, dtype=torch.float64, pin_memory=True)
+        ou = torch.empty(uu.shape, dtype=torch.float64, pin_memory=True)
+        pin.append((pp, a.numpy(), b.numpy(), on.numpy(), ou.numpy()))
+    h2d = sum(a.nbytes + b.nbytes for _, a, b, _, _ in pin)
+    d2h = sum(a.nbytes + b.nbytes for _, _, _, a, b in pin)
+    be = w.wdlb_batch_create(len(pores), pool + (1 << 20), storage="f32")
+
+    def e2e_step():
+        ss = [w.wdlb_batch_add(be, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"], pp["tau"], pp["g"], a, b)
+              for pp, a, b, _, _ in pin]
+        w.wdlb_batch_step(be, SUB)
+        for s, (_, _, _, on, ou) in zip(ss, pin):
+            w.wdlb_moments(w.wdlb_batch_context(be, s), on, ou)
+        for s in ss:
+            w.wdlb_batch_remove(be, s)
+
+    e2e_steps = max(2, args.steps // 4)
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    w.wdlb_batch_destroy(be)
+    e2e_value = job_mlups(world, nodes_b, SUB * e2e_steps, e2e_s)
+    assert all(np.isfinite(on).all() for _, _, _, on, _ in pin)
+
+    # ---------------- the 128^3 bulk box (device-resident) ----------------
     p, n_h, u_h = synth.bulk_shear_128(seed=2 + rank, sigma=SIGMA)
     N = L ** 3
     shape = (p["nx"], p["ny"], p["nz"])
@@ -372,112 +593,65 @@ def run_ours(args):
         ctx.stream.synchronize()
         return ctx
 
-    # ---------------- device-resident timed region (FP32 path) ----------------
-    ctx = make("f32", args.shell_rule)
-    tile_info = w.wdlb_tile_info(ctx)
-    # the production path: wdlb_step (CUDA-graph replays of 50 time steps) and the
-    # FP64 pore-average reduction, as a user steps a lattice
-    for _ in range(args.warmup):
-        w.wdlb_step(ctx, SUB)
-        w.wdlb_pore_average(ctx)
-    w.wdlb_profile_step(ctx, SUB)
-    sampler = ClockSampler(local)
-    if rank == 0:
-        sampler.start()
-        time.sleep(0.3)
-    launches0 = w.wdlb_launch_count(ctx)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    ev0.record(ctx.stream)
-    for _ in range(args.steps):
-        w.wdlb_step(ctx, SUB)
-        w.wdlb_pore_average(ctx)
-    ev1.record(ctx.stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop() if rank == 0 else None
-    gpu_launches = w.wdlb_launch_count(ctx) - launches0
-    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
-    value = job_mlups(world, N, SUB * args.steps, elapsed_ms * 1e-3)
-    # per-kernel durations for the roofline: the same workload stepped kernel by
-    # kernel with CUDA events around every launch on the context's stream
-    kms = [0.0, 0.0, 0.0]
-    ia = torch.cuda.Event(enable_timing=True)
-    ib = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ia.record(ctx.stream)
-    for _ in range(args.steps):
-        ms = w.wdlb_profile_step(ctx, SUB)
-        for k in range(3):
-            kms[k] += ms[k] / args.steps
-    ib.record(ctx.stream)
-    torch.cuda.synchronize()
-    instrumented_ms = max_over_ranks(ia.elapsed_time(ib)) / args.steps
-    stats = w.wdlb_pore_average(ctx)
-    if args.only_device:
-        if rank == 0:
-            print(json.dumps({"only_device": True, "value": value, "unit": UNIT, "ms_per_step": elapsed_ms / args.steps,
-                              "time_steps_per_step": SUB, "kernels_ms": kms, "instrumented_ms_per_step": instrumented_ms,
-                              "gpu_launches": int(gpu_launches), "tile_shape": tile_info[1]}),
-                  flush=True)
-        if dist is not None:
-            dist.destroy_process_group()
-        return 0
+    def box_leg(storage, rule, sub, reps):
+        c2 = make(storage, rule)
+        w.wdlb_step(c2, sub)
+        pk = [0.0, 0.0, 0.0]
+        for _ in range(reps):          # per-kernel durations (instrumented pass)
+            ms = w.wdlb_profile_step(c2, sub)
+            for k in range(3):
+                pk[k] += ms[k] / reps
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(c2.stream)
+        for _ in range(reps):          # throughput: the production path
+            w.wdlb_step(c2, sub)
+            w.wdlb_pore_average(c2)
+        b.record(c2.stream)
+        torch.cuda.synchronize()
+        t = max_over_ranks(a.elapsed_time(b))
+        mlups = job_mlups(world, N, sub * reps, t * 1e-3)
+        out = {"value": mlups, "unit": UNIT, "kernels_ms": pk, "tile_shape": w.wdlb_tile_info(c2)[1],
+               "hbm_frac_of_measured": mlups * 1e6 * BYTES_PER_NODE[storage] / 1e9 / peaks["hbm_gbs"]}
+        if storage == "f32":
+            ns = len(w.wdlb_shell_table(SIGMA, rule)[1]) if rule == "compact" else shell_size(SIGMA)
+            fl = ns * (FLOPS_PER_PAIR_WEIGHTED if rule == "compact" else FLOPS_PER_PAIR) + FLOPS_COLLIDE
+            tf = fl * N / (pk[2] * 1e-3) / 1e12
+            out.update({"shell_vectors": ns, "flops_per_node": fl, "shell_kernel_alu_frac": tf / alu_peak,
+                        "shell_kernel_tflops": tf,
+                        "shell_kernel_hbm_frac_of_measured": BYTES_PER_NODE[storage] * N / (pk[2] * 1e-3)
+                        / 1e9 / peaks["hbm_gbs"]})
+        w.wdlb_destroy(c2)
+        return out
 
-    # ---------------- end to end through host buffers ----------------
-    pin_n = torch.empty(n_h.shape, dtype=torch.float64, pin_memory=True)
-    pin_u = torch.empty(u_h.shape, dtype=torch.float64, pin_memory=True)
-    pin_n.copy_(torch.from_numpy(n_h))
-    pin_u.copy_(torch.from_numpy(u_h))
-    out_n = torch.empty(n_h.shape, dtype=torch.float64, pin_memory=True)
-    out_u = torch.empty(u_h.shape, dtype=torch.float64, pin_memory=True)
-    hn, hu, on, ou = pin_n.numpy(), pin_u.numpy(), out_n.numpy(), out_u.numpy()
-    e2e_steps = max(2, args.steps // 2)
-    for _ in range(1):
-        w.wdlb_init_fields(ctx, hn, hu)
-        w.wdlb_step(ctx, SUB)
-        w.wdlb_moments(ctx, on, ou)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        w.wdlb_init_fields(ctx, hn, hu)
-        w.wdlb_step(ctx, SUB)
-        w.wdlb_moments(ctx, on, ou)
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    barrier()
-    e2e_value = job_mlups(world, N, SUB * e2e_steps, e2e_s)
-    assert np.isfinite(on).all()
+    paths = {}
+    for name, storage, rule, sub, reps in (("bulk128_f32", "f32", args.shell_rule, SUB, max(3, args.steps // 2)),
+                                           ("bulk128_f32_compact_shell", "f32", "compact", SUB, 3),
+                                           ("bulk128_f16", "f16", "full", SUB, 3),
+                                           ("bulk128_f64", "f64", "full", 10, 2)):
+        paths[name] = box_leg(storage, rule, sub, reps)
 
-    # ---------------- batched slit pores (one launch per phase for all pores) ----------------
-    pores = synth.batched_pores()
-    nodes_b = sum(pp["nx"] * pp["ny"] * pp["nz"] for pp, _, _ in pores)
-    pool = 0
-    probe = w.wdlb_batch_create(1, 1 << 20, storage="f32")
-    for pp, _, _ in pores:
-        pool += (w.wdlb_batch_pore_bytes(probe, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"]) + 255) // 256 * 256
-    w.wdlb_batch_destroy(probe)
-    bt = w.wdlb_batch_create(len(pores), pool + (1 << 20), storage="f32")
-    for pp, nn, uu in pores:
-        w.wdlb_batch_add(bt, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"], pp["tau"], pp["g"], nn, uu)
-    w.wdlb_batch_step(bt, 20)
-    bt.stream.synchronize()
-    ba = torch.cuda.Event(enable_timing=True)
-    bb = torch.cuda.Event(enable_timing=True)
-    breps = max(2, args.steps // 2)
-    bl0 = w.wdlb_batch_launch_count(bt)
-    ba.record(bt.stream)
-    for _ in range(breps):
-        w.wdlb_batch_step(bt, SUB)
-    bb.record(bt.stream)
+    # ---------------- the full-size slit 256 x 256 x 161 (FP32) ----------------
+    sp, sn, su = synth.slit_poiseuille(256, 256, 161, 0.3, SIGMA, 0.8, 1e-6, seed=3)
+    cs = w.wdlb_create((256, 256, 161), SIGMA, True, 0.8, sp["g"], storage="f32")
+    w.wdlb_init_fields(cs, sn, su)
+    w.wdlb_step(cs, 50)
+    pk = w.wdlb_profile_step(cs, 20)
     torch.cuda.synchronize()
-    bt_ms = max_over_ranks(ba.elapsed_time(bb))
-    batched = {"value": job_mlups(world, nodes_b, SUB * breps, bt_ms * 1e-3), "unit": UNIT, "pores": len(pores),
-               "nodes": nodes_b, "time_steps": SUB * breps, "gpu_launches": w.wdlb_batch_launch_count(bt) - bl0,
-               "workload": "64 slit pores 32x32x(13..121), sigma=4, n* in [0.1, 0.6], g_x log-uniform "
-                           "[1e-7, 1e-5], tau=1, FP32; one launch per phase for all pores, CUDA graph"}
-    w.wdlb_batch_destroy(bt)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(cs.stream)
+    w.wdlb_step(cs, 200)
+    w.wdlb_pore_average(cs)
+    b.record(cs.stream)
+    torch.cuda.synchronize()
+    Ns = 256 * 256 * 161
+    paths["slit_256x256x161_f32"] = {"value": job_mlups(world, Ns, 200, max_over_ranks(a.elapsed_time(b)) * 1e-3),
+                                     "unit": UNIT, "kernels_ms": pk, "tile_shape": w.wdlb_tile_info(cs)[1],
+                                     "workload": "slit 256x256x161, walls z=0,160, sigma=4, n*=0.3, tau=0.8, "
+                                                 "g_x=1e-6, FP32; 200 time steps + pore average"}
+    w.wdlb_destroy(cs)
 
     # ---------------- serving: Poisson arrivals of steady-state slit solves ----------------
     serve = None
@@ -498,7 +672,6 @@ def run_ours(args):
             res = sweeps.pore_viscosity_sweep(chi, widths)
             sweep["ratio_chi_%g" % chi] = [round(r["ratio"], 5) if r["status"] == 0 else None for r in res]
         dt = time.perf_counter() - t0
-        # the compact contact shell on the dilute pore (chi 0.32 is above its density limit)
         t1 = time.perf_counter()
         cres_p = sweeps.pore_viscosity_sweep(0.11, widths, shell_rule="compact")
         sweep["ratio_chi_0.11_compact_shell"] = [round(r["ratio"], 5) if r["status"] == 0 else None for r in cres_p]
@@ -506,7 +679,6 @@ def run_ours(args):
         sweep["solves"] = 2 * len(widths)
         sweep["seconds"] = dt
         sweep["solves_per_s"] = 2 * len(widths) / dt
-        # bulk viscosity against packing fraction (Sec. 5, Fig. 1's experiment), sigma 8
         t0 = time.perf_counter()
         bres = sweeps.bulk_viscosity_sweep([0.05, 0.1, 0.15, 0.2, 0.25, 0.3, 0.35])
         sweep["bulk_sigma8"] = {"chi": [r["chi"] for r in bres if r["K"] == 2.0],
@@ -526,68 +698,25 @@ def run_ours(args):
             "over_full_shell_K2": [round(c["eta"] / f["eta"], 5) for c, f in zip(cres, bres) if c["K"] == 2.0],
             "seconds": time.perf_counter() - t0}
 
-    # ---------------- other storage paths and the compact shell (same workload, shorter) ----------------
-    paths = {}
-    for name, storage, rule, sub, reps in (("f64", "f64", "full", 10, 2), ("f16", "f16", "full", SUB, 3),
-                                           ("f32_compact_shell", "f32", "compact", SUB, 3)):
-        c2 = make(storage, rule)
-        w.wdlb_step(c2, sub)
-        pk = [0.0, 0.0, 0.0]
-        for _ in range(reps):          # per-kernel durations (instrumented pass)
-            ms = w.wdlb_profile_step(c2, sub)
-            for k in range(3):
-                pk[k] += ms[k] / reps
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(c2.stream)
-        for _ in range(reps):          # throughput: the production path
-            w.wdlb_step(c2, sub)
-        b.record(c2.stream)
-        torch.cuda.synchronize()
-        t = max_over_ranks(a.elapsed_time(b))
-        mlups = job_mlups(world, N, sub * reps, t * 1e-3)
-        paths[name] = {"value": mlups, "unit": UNIT, "kernels_ms": pk,
-                       "hbm_frac_of_measured": mlups * 1e6 * BYTES_PER_NODE[storage] / 1e9
-                       / measured_peaks()[0]["hbm_gbs"]}
-        if rule == "compact":
-            ns = len(w.wdlb_shell_table(SIGMA, "compact")[1])
-            fl = ns * FLOPS_PER_PAIR_WEIGHTED + FLOPS_COLLIDE
-            alu = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-            tf = fl * N / (pk[2] * 1e-3) / 1e12
-            paths[name].update({"shell_vectors": ns, "full_shell_vectors": shell_size(SIGMA),
-                                "tile_shape": w.wdlb_tile_info(c2)[1], "flops_per_node": fl,
-                                "shell_kernel_alu_frac": tf / alu, "shell_kernel_tflops": tf,
-                                "shell_kernel_hbm_frac_of_measured": BYTES_PER_NODE[storage] * N / (pk[2] * 1e-3)
-                                / 1e9 / measured_peaks()[0]["hbm_gbs"]})
-        w.wdlb_destroy(c2)
-
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    # ---------------- roofline of the dominant kernel ----------------
-    peaks, peak_kind = measured_peaks()
-    if args.shell_rule == "compact":
-        nshell = len(w.wdlb_shell_table(SIGMA, "compact")[1])
-        flops_per_node = nshell * FLOPS_PER_PAIR_WEIGHTED + FLOPS_COLLIDE
-    else:
-        nshell = shell_size(SIGMA)
-        flops_per_node = nshell * FLOPS_PER_PAIR + FLOPS_COLLIDE
+    # ---------------- roofline of the dominant kernel (the batch's shell phase) ----------------
+    nshell = shell_size(BATCH_SIGMA)
+    flops_per_node = nshell * FLOPS_PER_PAIR + FLOPS_COLLIDE
     shell_ms = kms[2]
-    achieved_tflops = flops_per_node * N / (shell_ms * 1e-3) / 1e12
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved_tflops = flops_per_node * nodes_b / (shell_ms * 1e-3) / 1e12
     step_ms = sum(kms)
-    hbm_achieved = BYTES_PER_NODE["f32"] * N / (step_ms * 1e-3) / 1e9
-    wt = "true" if args.shell_rule == "compact" else "false"
-    kname = (("k_step_shell_tiled<float, %d, %d, false, %s>" % (int(round(2 * SIGMA)), tile_info[1], wt)) if tile_info[0]
-             else "k_step_shell<float, 0, false, %s>" % wt)
+    hbm_achieved = BYTES_PER_NODE["f32"] * nodes_b / (step_ms * 1e-3) / 1e9
+    kname = ", ".join("k_step_shell_tiled<float, %d, %d, true, false>" % (int(round(2 * BATCH_SIGMA)), t[1]) if t[0]
+                      else "k_step_shell<float, 0, true, false>" for t in tiles)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved_tflops, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak,
-                "traffic": recorded_traffic() if args.shell_rule == "full" and SIGMA == 4.0 else None,
-                "peak_source": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2070 MHz (recipe unit counts)",
-                "flops_per_node": flops_per_node,
+                "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak, "traffic": recorded_traffic(nodes_b),
+                "peak_source": "FP32 FMA issue: %d SMs (queried) x 128 lanes x 2 x 2070 MHz (recipe unit counts)"
+                               % sm_count,
+                "flops_per_node": flops_per_node, "nodes_per_launch": nodes_b,
                 "share_of_step": shell_ms / step_ms if step_ms > 0 else None,
                 "hbm": {"achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": hbm_achieved / peaks["hbm_gbs"], "peak_source": peak_kind,
@@ -600,23 +729,25 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes": N, "time_steps_per_step": SUB,
-                       "storage": "f32 deviation from w_q n_ref, FP64 reductions",
-                       "l2": "no flush: populations 2 x 159 MB + fields exceed the 129 MB L2",
+            "config": {"workload": BATCH_WORKLOAD, "pores": len(pores), "nodes": nodes_b,
+                       "time_steps_per_step": SUB,
+                       "step": "%d time steps of every pore (CUDA-graph replays) + the FP64 flux residual of "
+                               "every pore" % SUB,
+                       "storage": "f32 deviation from the local rest state, FP64 reductions",
+                       "l2": "no flush: populations 2 x %.0f MB exceed the 129 MB L2" % (nodes_b * 76 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "shell_rule": args.shell_rule,
-                       "shell_kernel": {"tiled": tile_info[0], "tile_shape": tile_info[1],
-                                        "chosen_by": "autotuner" if args.tile < 0 else "--tile"}},
+                       "shell_kernel": {"tiles": tiles, "chosen_by": "autotuner (built-in rule)"},
+                       "sm_count": sm_count},
             "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hn.nbytes + hu.nbytes),
-                    "d2h_bytes_per_step": int(on.nbytes + ou.nbytes),
-                    "path": "wdlb_init_fields(host) + wdlb_step(100) + wdlb_moments(host), pinned buffers"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "path": "per step: wdlb_batch_add of the 64 pores from pinned host n, u; wdlb_batch_step(%d); "
+                            "wdlb_moments of every pore into pinned host buffers; wdlb_batch_remove" % SUB},
             "clocks": clocks, "gpu_launches": int(gpu_launches),
             "kernels_ms": {"moments": kms[0], "smeared_density": kms[1], "shell_collide_stream": kms[2],
-                           "source": "a second pass of the same workload launched kernel by kernel with CUDA events "
+                           "source": "a second pass of the same batch launched phase by phase with CUDA events "
                                      "around each launch (%.2f ms per bench step, against %.2f ms for the graph "
                                      "replays timed for value)" % (instrumented_ms, elapsed_ms / args.steps)},
-            "paths": paths, "batched": batched, "serve": serve, "pore_viscosity_sweep": sweep, "pore_average": {k: stats[k] for k in ("mass", "mean_n", "mean_ux", "steps")}}
+            "paths": paths, "serve": serve, "pore_viscosity_sweep": sweep}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -306,6 +306,12 @@ wdlb_status wdlb_batch_add(wdlb_batch *b, const wdlb_pore_desc *d, const double 
 wdlb_status wdlb_batch_remove(wdlb_batch *b, int32_t slot);
 /* Steps 2-5 of the algorithm of Sec. 5 for every pore, nsteps times (async). */
 wdlb_status wdlb_batch_step(wdlb_batch *b, int64_t nsteps);
+/* nsteps time steps of every pore of the batch, launched kernel by kernel
+ * (moments, smeared density, every shell group) with CUDA events around each
+ * phase on the batch stream; ms[0..2] = average device time per step of each
+ * phase.  Same kernels, order and results as wdlb_batch_step; blocks until done.
+ * For measurement (no counterpart in the paper). */
+wdlb_status wdlb_batch_profile_step(wdlb_batch *b, int64_t nsteps, double ms[3]);
 /* Per slot (array of max_pores): the FP64 steady-state residual of
  * wdlb_run_steady, |Q - Q(previous call)| / (interval |Q|) with Q the pore flux
  * (+inf at a pore's first call, NaN for empty slots), and the slot status
@@ -369,6 +375,10 @@ wdlb_status wdlb_server_create(const wdlb_options *opt, uint64_t hbm_budget, int
 wdlb_status wdlb_server_submit(wdlb_server *s, const wdlb_request *r, int64_t *id);
 /* Move up to cap finished results into out; returns how many. */
 int32_t wdlb_server_poll(wdlb_server *s, wdlb_result *out, int32_t cap);
+/* Counters of the server (thread-safe).  active, pool_free and launches are
+ * the batch's values as the worker thread last published them (after each
+ * admission round and each block of steps); the worker owns the batch, and
+ * this call never reads it. */
 wdlb_status wdlb_server_info(wdlb_server *s, wdlb_server_stats *info);
 /* Stop the worker (unfinished requests are dropped) and free everything. */
 void wdlb_server_destroy(wdlb_server *s);
@@ -390,13 +400,23 @@ void wdlb_server_destroy(wdlb_server *s);
  * process exits; the call allocates and frees nothing.  Lattices with more
  * than WDLB_STATIC_MAX_NODES nodes, or sigma outside [1, 8], are rejected with
  * WDLB_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) on the current device; make that first call
- * before any stream capture.  All work is enqueued on `stream` (a
+ * address (cudaGetSymbolAddress) on the current device and keeps it for the
+ * later calls on that device; make that first call before any stream capture.
+ * The kept address belongs to the device's current context: after a
+ * cudaDeviceReset it is no longer valid.  All work is enqueued on `stream` (a
  * cudaStream_t, NULL = legacy default stream); the stencil tables are copied
- * from pageable host memory, so the call may wait for work already queued on
- * that stream.  Every call shares the one array and the array keeps the last
- * call's contents: calls that overlap on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller. */
+ * from pageable host memory.  The call then waits for its work on `stream` to
+ * finish and reads back the status word its kernels set in the array:
+ *   WDLB_OK            nbar, C and A are written;
+ *   WDLB_ERR_UNSTABLE  the state is not physical: a smeared packing fraction
+ *                      >= 1, a negative or non-finite density or a non-finite
+ *                      velocity at a fluid node (the outputs are not meaningful);
+ *   WDLB_ERR_CUDA      a CUDA call failed, or (bounds-checked build only) a
+ *                      kernel index left its array and the access was skipped.
+ * Every call shares the one array and the array keeps the last call's
+ * contents (the status word is cleared at the start of each call): calls that
+ * overlap on the GPU (other streams, other host threads) race on it and must
+ * be serialised by the caller. */
 #define WDLB_STATIC_MAX_NODES 262144
 wdlb_status wdlb_fields_static(wdlb_lattice lat, double sigma, int32_t walls, int32_t closure,
                                const double *d_n, const double *d_u, double *d_nbar, double *d_C,

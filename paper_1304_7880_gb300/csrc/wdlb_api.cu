@@ -1470,6 +1470,47 @@ wdlb_status wdlb_batch_step(wdlb_batch *b, int64_t nsteps)
     return WDLB_OK;
 }
 
+wdlb_status wdlb_batch_profile_step(wdlb_batch *b, int64_t nsteps, double ms[3])
+{
+    TraceRange tr("wdlb_batch_profile_step");
+    if (!b || !ms || nsteps < 1) return WDLB_ERR_ARG;
+    if (b->dirty) {
+        wdlb_status s = batch_build(b);
+        if (s != WDLB_OK) return s;
+    }
+    std::vector<cudaEvent_t> ev(6 * nsteps, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto &x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    for (int64_t s = 0; s < nsteps && e == cudaSuccess; s++) {
+        const int parity = (int)(b->steps_since_build & 1);
+        for (int part = 0; part < 3 && e == cudaSuccess; part++) {
+            e = cudaEventRecord(ev[6 * s + 2 * part], b->stream);
+            if (e == cudaSuccess) e = b->L->batch_step(b->launch, parity, part, -1, b->stream, &b->launches);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[6 * s + 2 * part + 1], b->stream);
+        }
+        if (e == cudaSuccess) b->steps_since_build++;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    double acc[3] = {0, 0, 0};
+    for (int64_t s = 0; s < nsteps && e == cudaSuccess; s++)
+        for (int part = 0; part < 3 && e == cudaSuccess; part++) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[6 * s + 2 * part], ev[6 * s + 2 * part + 1]);
+            acc[part] += t;
+        }
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch profile step: %s", cudaGetErrorString(e));
+    for (auto &sl : b->slots)
+        if (sl.ctx) {
+            sl.ctx->cur ^= (int)(nsteps & 1);
+            sl.ctx->steps += nsteps;
+        }
+    for (int k = 0; k < 3; k++) ms[k] = acc[k] / double(nsteps);
+    return WDLB_OK;
+}
+
 wdlb_status wdlb_batch_residuals(wdlb_batch *b, int32_t interval, double *res, int32_t *status)
 {
     if (!b || interval < 1) return WDLB_ERR_ARG;
@@ -1587,6 +1628,11 @@ struct wdlb_server {
     std::vector<wdlb_result> done;
     int64_t next_id = 1, submitted = 0, admitted = 0, completed = 0;
     int64_t node_steps = 0;       // lattice-node updates executed
+    // the batch's counters as the worker last saw them (read under mu by
+    // wdlb_server_info, which must not touch the batch the worker mutates)
+    int32_t snap_active = 0;
+    uint64_t snap_free = 0;
+    int64_t snap_launches = 0;
     std::chrono::steady_clock::time_point t0;
     std::string err;
 };
@@ -1596,6 +1642,18 @@ namespace {
 double server_now(const wdlb_server *s)
 {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+}
+
+// Worker thread only: copy the batch's counters into the snapshot.
+void server_publish(wdlb_server *s)
+{
+    const int32_t active = wdlb_batch_active(s->batch);
+    const uint64_t free_bytes = wdlb_batch_free_bytes(s->batch);
+    const int64_t launches = wdlb_batch_launch_count(s->batch);
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->snap_active = active;
+    s->snap_free = free_bytes;
+    s->snap_launches = launches;
 }
 
 void server_finish(wdlb_server *s, int slot, int32_t status, double residual)
@@ -1696,6 +1754,7 @@ void server_loop(wdlb_server *s)
         }
         // u_x snapshot of the new pores (the others' snapshots are re-taken at the same state)
         if (admitted_now) wdlb_batch_residuals(s->batch, s->check_every, res.data(), st.data());
+        server_publish(s);
         if (wdlb_batch_active(s->batch) == 0) continue;
         int64_t block_nodes = 0;
         for (size_t k = 0; k < s->active.size(); k++)
@@ -1726,6 +1785,7 @@ void server_loop(wdlb_server *s)
             else if (c && c->steps >= q.max_steps)
                 server_finish(s, (int)k, WDLB_ERR_TIMEOUT, res[k]);
         }
+        server_publish(s);
     }
 }
 
@@ -1757,6 +1817,7 @@ wdlb_status wdlb_server_create(const wdlb_options *opt, uint64_t hbm_budget, int
     s->check_every = check_every;
     s->active.resize(max_active);
     for (auto &a : s->active) a.id = 0;
+    s->snap_free = wdlb_batch_free_bytes(s->batch);
     s->t0 = std::chrono::steady_clock::now();
     s->worker = std::thread(server_loop, s);
     *out = s;
@@ -1803,9 +1864,9 @@ wdlb_status wdlb_server_info(wdlb_server *s, wdlb_server_stats *info)
     info->admitted = s->admitted;
     info->completed = s->completed;
     info->queued = (int64_t)s->queue.size();
-    info->active = wdlb_batch_active(s->batch);
-    info->pool_free = wdlb_batch_free_bytes(s->batch);
-    info->launches = wdlb_batch_launch_count(s->batch);
+    info->active = s->snap_active;
+    info->pool_free = s->snap_free;
+    info->launches = s->snap_launches;
     info->clock_s = server_now(s);
     info->node_steps = s->node_steps;
     return WDLB_OK;

@@ -115,7 +115,11 @@ __global__ void __launch_bounds__(256) k_static_prepare(KParams p0, StaticBufs s
         s.nu[i] = V4<float>{-float(p.n_off), 0.f, 0.f, 0.f};
         return;
     }
-    s.nu[i] = V4<float>{float(d_n[i] - p.n_off), float(d_u[i]), float(d_u[p.N + i]), float(d_u[2 * p.N + i])};
+    const double n = d_n[i], ux = d_u[i], uy = d_u[p.N + i], uz = d_u[2 * p.N + i];
+    // a negative or non-finite density, or a non-finite velocity, is not a state
+    if (!(n >= 0.0) || !isfinite(n) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz))
+        atomicOr(s.status, kStatusUnstable);
+    s.nu[i] = V4<float>{float(n - p.n_off), float(ux), float(uy), float(uz)};
 }
 
 __global__ void __launch_bounds__(256) k_static_ball(KParams p0, StaticBufs s)
@@ -246,5 +250,15 @@ extern "C" wdlb_status wdlb_fields_static(wdlb_lattice lat, double sigma, int32_
         launch_fields<1>(walls != 0, blocks, st, p, s, d_nbar, d_C, d_A);
     else
         launch_fields<2>(walls != 0, blocks, st, p, s, d_nbar, d_C, d_A);
-    return cudaGetLastError() == cudaSuccess ? WDLB_OK : WDLB_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return WDLB_ERR_CUDA;
+    // the status word the kernels set, read back after they finish: bit 1 a
+    // non-physical state (smeared packing fraction >= 1, bad n or u), bit 2
+    // (checked build only) an index outside its array, whose access was skipped
+    int h = 0;
+    if (cudaMemcpyAsync(&h, s.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return WDLB_ERR_CUDA;
+    if (h & kStatusBounds) return WDLB_ERR_CUDA;
+    if (h) return WDLB_ERR_UNSTABLE;
+    return WDLB_OK;
 }

@@ -95,8 +95,9 @@ def batched_pores(count: int = 64, seed: int = 4, sigma: float = 4.0, nxy: int =
     """Batch of slit pores: H uniform in [3 sigma, 30 sigma] (nz = H + 1),
     n* uniform in [0.1, n_star_max], g_x log-uniform in [1e-7, 1e-5], tau = 1.
     (Densities up to n* = 0.8 exceed the scheme's stability: its uniform
-    fluid is linearly unstable above n* ~ 0.65, so the default upper end is
-    0.6.)"""
+    fluid is linearly unstable above n* ~ 0.71 at sigma 4, and slits, whose
+    wall layers are far denser than the mean, hold to n* ~ 0.6, the default
+    upper end.)"""
     U = uniform01(seed, 3 * count).reshape(count, 3)
     out = []
     for p in range(count):

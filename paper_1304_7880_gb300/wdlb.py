@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH):
         "wdlb_batch_add": (I32, [P, P, P, P, P]),
         "wdlb_batch_remove": (I32, [P, I32]),
         "wdlb_batch_step": (I32, [P, I64]),
+        "wdlb_batch_profile_step": (I32, [P, I64, P]),
         "wdlb_batch_residuals": (I32, [P, I32, P, P]),
         "wdlb_batch_context": (P, [P, I32]),
         "wdlb_batch_active": (I32, [P]),
@@ -366,13 +367,38 @@ def wdlb_profile_step(ctx: Context, nsteps: int):
 WDLB_STATIC_MAX_NODES = 262144
 
 
+def _check_device_tensor(call, name, t, count):
+    """A float64 tensor on the current CUDA device, contiguous, of `count`
+    elements; WDLBError(ERR_ARG) otherwise."""
+    import torch
+    ok = (isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+          and t.numel() == count)
+    if ok and t.device.index != torch.cuda.current_device():
+        ok = False
+    if not ok:
+        desc = ("%s %s on %s, %d elements" % (type(t).__name__, getattr(t, "dtype", "?"), getattr(t, "device", "?"),
+                                                getattr(t, "numel", lambda: -1)()))
+        raise WDLBError(1, "%s: %s must be a contiguous float64 tensor of %d elements on the current CUDA device "
+                           "(got %s)" % (call, name, count, desc))
+
+
 def wdlb_fields_static(lattice, sigma, walls, closure, d_n, d_u, d_nbar, d_C, d_A, stream=None):
     """Fields (nbar, C, A) of device arrays n, u without any device allocation
     (see include/wdlb.h): torch CUDA tensors of float64, results written into
     d_nbar (may be None), d_C, d_A; enqueued on `stream` (torch.cuda.Stream or
     None for the legacy default stream)."""
-    lib = load_library()
     nx, ny, nz = (int(v) for v in lattice)
+    N = nx * ny * nz
+    # the C side cannot see a buffer's type or size: a wrong one would be
+    # read or written past its end, so every tensor is checked here first
+    for name, t, count, required in (("n", d_n, N, True), ("u", d_u, 3 * N, True), ("nbar", d_nbar, N, False),
+                                     ("C", d_C, 3 * N, True), ("A", d_A, 6 * N, True)):
+        if t is None:
+            if required:
+                raise WDLBError(1, "wdlb_fields_static: %s is required" % name)
+            continue
+        _check_device_tensor("wdlb_fields_static", name, t, count)
+    lib = load_library()
     ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
     st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     _check(lib.wdlb_fields_static(wdlb_lattice(nx, ny, nz), float(sigma), 1 if walls else 0, CLOSURES[closure],
@@ -482,6 +508,15 @@ def wdlb_batch_remove(batch, slot):
 
 def wdlb_batch_step(batch, nsteps=1):
     _bcheck(load_library().wdlb_batch_step(batch.handle, int(nsteps)), batch)
+
+
+def wdlb_batch_profile_step(batch, nsteps=1):
+    """nsteps time steps launched kernel by kernel with CUDA events around each
+    phase; returns the average ms per step of (moments, smeared density, shell
+    sums + collision + streaming)."""
+    ms = (ctypes.c_double * 3)()
+    _bcheck(load_library().wdlb_batch_profile_step(batch.handle, int(nsteps), ms), batch)
+    return [ms[0], ms[1], ms[2]]
 
 
 def wdlb_batch_residuals(batch, interval):

@@ -77,6 +77,15 @@ def main(out):
     res["fields_C"] = C
     res["fields_A"] = A
     w.wdlb_destroy(ctx)
+    # the entry point without device allocation (generic kernels, sigma 8 with walls)
+    import torch
+    lat = (9, 8, 14)
+    n, u = state(lat, 8.0, True, 13)
+    d_n, d_u = torch.from_numpy(n).cuda(), torch.from_numpy(u).cuda()
+    outs = [torch.empty(k * n.size, dtype=torch.float64, device="cuda") for k in (1, 3, 6)]
+    w.wdlb_fields_static(lat, 8.0, True, "PY", d_n, d_u, *outs)   # raises on the bounds flag
+    torch.cuda.synchronize()
+    res["static_nbar"], res["static_C"], res["static_A"] = (t.cpu().numpy() for t in outs)
     np.savez(out, **res)
     print("checked cases: %d arrays, library %s" % (len(res), os.path.basename(w.LIB_PATH)))
 

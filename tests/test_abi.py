@@ -126,3 +126,25 @@ def test_workspace_size_scales_with_storage(lib):
     N = 32 ** 3
     assert sizes["f64"] > sizes["f32"] > sizes["f16"]
     assert sizes["f32"] - sizes["f16"] >= 2 * 19 * N * 2 * 0.99
+
+
+def test_fields_static_binding_checks_its_tensors():
+    """The binding of wdlb_fields_static refuses, before any library call, a
+    tensor of the wrong type, size or device: the C side cannot see a buffer's
+    extent, and a wrong one would be read or written past its end."""
+    torch = pytest.importorskip("torch")
+    from paper_1304_7880_gb300 import wdlb as w
+    lat = (4, 3, 5)
+    N = 60
+    bad = [
+        (torch.zeros(N, dtype=torch.float32), torch.zeros(3 * N, dtype=torch.float64)),   # float32 n
+        (torch.zeros(N, dtype=torch.float64), torch.zeros(3 * N - 1, dtype=torch.float64)),  # short u
+        (torch.zeros(N, dtype=torch.float64), torch.zeros(3 * N, dtype=torch.float64)),   # host memory
+    ]
+    for d_n, d_u in bad:
+        with pytest.raises(w.WDLBError) as ei:
+            w.wdlb_fields_static(lat, 4.0, False, "CS", d_n, d_u, None, torch.zeros(3 * N, dtype=torch.float64),
+                                 torch.zeros(6 * N, dtype=torch.float64))
+        assert ei.value.status == 1
+    with pytest.raises(w.WDLBError):
+        w.wdlb_fields_static(lat, 4.0, False, "CS", None, None, None, None, None)
