@@ -3,7 +3,7 @@
 
 Headline workload: 64 slit pores in one batch (widths H uniform in [3 sigma,
 30 sigma] at sigma = 4, i.e. 13-121 z-nodes, x-y 32 x 32, n* uniform in
-[0.1, 0.6], g_x log-uniform in [1e-7, 1e-5], tau = 1), FP32 deviation storage
+[0.1, 0.57], g_x log-uniform in [1e-7, 1e-5], tau = 1), FP32 deviation storage
 with FP64 reductions.  One benchmark step = 100 lattice time steps of every
 pore (each: moments and field velocity, smeared density, shell sums +
 collision + streaming; one launch per phase for all pores, replayed from a
@@ -45,7 +45,7 @@ SUB = 100                      # lattice time steps per benchmark step
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 BATCH_WORKLOAD = ("64 slit pores 32x32x(13..121) (H uniform in [3 sigma, 30 sigma]), sigma=4 lattice units, "
-                  "walls z=0 and z=nz-1, n* uniform in [0.1, 0.6] (the scheme's stability limit in slits), "
+                  "walls z=0 and z=nz-1, n* uniform in [0.1, 0.57] (below the scheme's stability limit in slits), "
                   "g_x log-uniform in [1e-7, 1e-5], tau=1, D3Q19, Carnahan-Starling contact value, K=2, "
                   "seeded 1e-3 density noise")
 WORKLOAD = ("bulk periodic box 128^3, sigma=4 lattice units, packing fraction 0.3, D3Q19, "
@@ -365,7 +365,7 @@ def run_serving(w, synth, np, rate, window_s, drain_s, max_active=48, tol=1e-8):
 
 
 SERVE_WORKLOAD = ("slit Poiseuille requests: sigma in {3,4,6}, H/sigma lognormal (median 10, log-sd 0.5) clipped "
-                  "to [3,60], x-y 16..64, n* in [0.1,0.6], g_x log-uniform [1e-7,1e-5], tau=1, FP32, steady "
+                  "to [3,60], x-y 16..64, n* in [0.1,0.57], g_x log-uniform [1e-7,1e-5], tau=1, FP32, steady "
                   "state at relative pore-flux change < 1e-8 per step (checked every 100 steps), 24 GiB "
                   "admission budget, FIFO admission, at most 48 pores stepped together")
 

@@ -331,6 +331,11 @@ __device__ __forceinline__ double fast_rcp<double>(double x)
     return 1.0 / x;
 }
 
+// a + b rounded as a sum: never contracted with a product into a multiply-add,
+// so the bits do not depend on how the surrounding code is compiled
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
 template <int CL, class T>
 __device__ __forceinline__ void pair_weights(T s0, T noff, T dhp, T dnp, T dhm, T dnm, T &qp, T &qm, T &qd)
 {
@@ -349,7 +354,7 @@ __device__ __forceinline__ void pair_weights(T s0, T noff, T dhp, T dnp, T dhm, 
         const T rp = fast_rcp<T>(sp2 * sp), rm = fast_rcp<T>(sm2 * sm);
         gp = fma(sp, rp, rp);
         gm = fma(sm, rm, rm);
-        gd = (dhp - dhm) * (sp2 + sm2 + fma(spm, sp + sm, spm)) * (rp * rm);
+        gd = (dhp - dhm) * (add_rn(sp2, sm2) + fma(spm, sp + sm, spm)) * (rp * rm);
     } else {
         const T rp = fast_rcp<T>(sp * sp), rm = fast_rcp<T>(sm * sm);
         gp = fma(-sp, rp, T(3) * rp);
@@ -387,7 +392,7 @@ __device__ __forceinline__ void accumulate_pair(ShellAcc<T> &a, T kx, T ky, T kz
     const T px = qp * vpx, py = qp * vpy, pz = qp * vpz;
     const T dx = fma(-qm, vmx, px), dy = fma(-qm, vmy, py), dz = fma(-qm, vmz, pz);
     const T ex = fma(qm, vmx, px), ey = fma(qm, vmy, py), ez = fma(qm, vmz, pz);
-    const T tq = qp + qm;
+    const T tq = add_rn(qp, qm);
     a.t += tq;
     const T sx = fma(-tq, vx, ex), sy = fma(-tq, vy, ey), sz = fma(-tq, vz, ez);
     a.Vx = fma(kx, qd, a.Vx); a.Vy = fma(ky, qd, a.Vy); a.Vz = fma(kz, qd, a.Vz);
@@ -486,6 +491,10 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
     const T uu = ux * ux + uy * uy + uz * uz;
     const T uF = ux * Fx + uy * Fy + uz * Fz;
     const T src_pref = T(1) - T(0.5) * omega;
+    // a node off the periodic edges of the lattice pushes to i + c_q without
+    // wrapping (with walls, z +- 1 of a fluid node is a fluid node or a wall)
+    const int nxy = nx * ny;
+    const bool inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && (WALLS || (z > 0 && z < nz - 1));
 
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
@@ -510,10 +519,14 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
             qq = opp_of(q);
             dn_t = dn_self;
         } else {
-            if (!WALLS) zt = wrap_coord(zt, nz);
-            const int xt = wrap_coord(x + cxq, nx);
-            const int yt = wrap_coord(y + cyq, ny);
-            dst = xt + nx * (yt + ny * zt);
+            if (inner) {
+                dst = i + cxq + cyq * nx + czq * nxy;
+            } else {
+                if (!WALLS) zt = wrap_coord(zt, nz);
+                const int xt = wrap_coord(x + cxq, nx);
+                const int yt = wrap_coord(y + cyq, ny);
+                dst = xt + nx * (yt + ny * zt);
+            }
             dn_t = q == 0 ? dn_self : target_dn(q, dst);
         }
         if (!in_bounds(dst, p.N, b.status)) continue;

@@ -4,6 +4,7 @@
 #include "wdlb_launch.h"
 #include "wdlb_shell_tiled.cuh"
 #include "wdlb_step_kernels.cuh"
+#include "wdlb_tables.h"
 
 #include <cstring>
 
@@ -121,6 +122,43 @@ void launch_tiled_v(const BatchLaunch &L, const KBufs<S, float> *B, const BatchG
 }
 #endif
 
+#if WDLB_STORAGE != 0
+// A compiled shell table (tiled::ct) is used only if it equals the library's
+// table for this sigma and rule: the same vectors in the same order, and for
+// the compact rule one weight per orbit.
+template <int S2, bool WT>
+bool compiled_table_matches()
+{
+    if constexpr (!tiled::ct::compiled<S2, WT>()) {
+        return true;
+    } else {
+        const double sigma = 0.5 * S2;
+        std::vector<int> e;
+        std::vector<double> wts;
+        double w = 0.0;
+        if (WT) {
+            if (!build_shell_compact(sigma, e, wts)) return false;
+        } else {
+            build_shell(sigma, e, &w);
+        }
+        constexpr tiled::ct::PairTable<S2, WT> T{};
+        if ((int)e.size() != 6 * T.n) return false;
+        for (int m = 0; m < T.n; m++) {
+            if (e[6 * m] != T.ex[m] || e[6 * m + 1] != T.ey[m] || e[6 * m + 2] != T.ez[m]) return false;
+            if (WT && wts[2 * m] != wts[2 * tiled::ct::first_pair_of_orbit<S2>(T.orb[m])]) return false;
+        }
+        return true;
+    }
+}
+
+template <int S2>
+bool table_ok(bool wt)
+{
+    static const bool full = compiled_table_matches<S2, false>(), compact = compiled_table_matches<S2, true>();
+    return wt ? compact : full;
+}
+#endif
+
 bool tiled_eligible(const KParams &p)
 {
 #if WDLB_STORAGE != 0
@@ -136,6 +174,7 @@ bool do_prepare(const KParams &p)
     if (!tiled_eligible(p) || p.tile < 0 || p.tile >= tiled::kVariants) return false;
 #if WDLB_STORAGE != 0
     const bool walls = p.walls != 0, wt = p.shell_rule != 0;
+    if (!(p.s2 == 6 ? table_ok<6>(wt) : (p.s2 == 8 ? table_ok<8>(wt) : table_ok<12>(wt)))) return false;
     cudaError_t e = p.s2 == 6 ? tiled_attr_r<6>(p.tile, walls, wt)
                               : (p.s2 == 8 ? tiled_attr_r<8>(p.tile, walls, wt) : tiled_attr_r<12>(p.tile, walls, wt));
     return e == cudaSuccess;

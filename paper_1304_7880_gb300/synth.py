@@ -91,13 +91,18 @@ def slit_poiseuille(nx, ny, nz, n_star, sigma, tau, gx, seed, amp=1e-3):
     return params, n, u
 
 
-def batched_pores(count: int = 64, seed: int = 4, sigma: float = 4.0, nxy: int = 32, n_star_max: float = 0.6):
+# Highest reduced density drawn for slit pores.  Densities up to n* = 0.8
+# exceed the scheme's stability: its uniform fluid is linearly unstable above
+# n* ~ 0.71 at sigma 4, and in slits the dense contact layer (n* ~ 1.5 at
+# contact) turns unstable in the wall plane first: wide slits hold to n* ~ 0.61
+# (sigma 3), 0.575 (sigma 4) and 0.59 (sigma 6).
+SLIT_N_STAR_MAX = 0.57
+
+
+def batched_pores(count: int = 64, seed: int = 4, sigma: float = 4.0, nxy: int = 32,
+                  n_star_max: float = SLIT_N_STAR_MAX):
     """Batch of slit pores: H uniform in [3 sigma, 30 sigma] (nz = H + 1),
-    n* uniform in [0.1, n_star_max], g_x log-uniform in [1e-7, 1e-5], tau = 1.
-    (Densities up to n* = 0.8 exceed the scheme's stability: its uniform
-    fluid is linearly unstable above n* ~ 0.71 at sigma 4, and slits, whose
-    wall layers are far denser than the mean, hold to n* ~ 0.6, the default
-    upper end.)"""
+    n* uniform in [0.1, n_star_max], g_x log-uniform in [1e-7, 1e-5], tau = 1."""
     U = uniform01(seed, 3 * count).reshape(count, 3)
     out = []
     for p in range(count):
@@ -109,7 +114,8 @@ def batched_pores(count: int = 64, seed: int = 4, sigma: float = 4.0, nxy: int =
     return out
 
 
-def serving_requests(rate: float, window_s: float, seed: int = 5, n_star_max: float = 0.6, ln_sigma: float = 0.5):
+def serving_requests(rate: float, window_s: float, seed: int = 5, n_star_max: float = SLIT_N_STAR_MAX,
+                     ln_sigma: float = 0.5):
     """Poisson arrivals (mean rate per second) over window_s seconds of slit
     Poiseuille requests: sigma in {3, 4, 6}; H/sigma lognormal with median 10
     and log-standard deviation ln_sigma, clipped to [3, 60]; nx = ny uniform in
