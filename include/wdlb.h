@@ -119,7 +119,22 @@ typedef struct {
                                  walls, nz, shell rule) key is seen; 0 use the
                                  built-in table                                     */
     int32_t shell_rule;       /* WDLB_SHELL_*, default FULL                          */
+    int32_t staging;          /* how the tiled shell kernel stages its field tile:
+                                 WDLB_STAGING_AUTO (default) one TMA box per array
+                                 for bricks whose tile needs no periodic wrap, where
+                                 the halo allows it (sigma 4, nx a multiple of 4),
+                                 per-node cp.async copies elsewhere;
+                                 WDLB_STAGING_CP_ASYNC per-node copies everywhere.
+                                 Both give bitwise the same tile                     */
+    int32_t wait_limit;       /* polls of the TMA tile's wait before the kernel gives
+                                 up, reports WDLB_ERR_TIMEOUT and skips the brick
+                                 (0: the default, ~4 million polls with short
+                                 sleeps).  Negative values are for tests of that
+                                 path: the kernel then issues no copy and waits on
+                                 a barrier that nothing completes, for -wait_limit
+                                 polls; the step's results are then not meaningful */
 } wdlb_options;
+enum { WDLB_STAGING_AUTO = 0, WDLB_STAGING_CP_ASYNC = 1 };
 
 enum { WDLB_TILE_AUTO = -1, WDLB_TILE_8x8x8 = 0, WDLB_TILE_8x8x8_WIDE = 1, WDLB_TILE_8x8x4 = 2 };
 
@@ -265,6 +280,12 @@ wdlb_status wdlb_autotune(wdlb_lattice lat, double sigma, int32_t walls, const w
 /* The shell kernel a context runs: *tiled 1 for the tiled kernel (then
  * *tile is its shape), 0 for the per-node kernel (*tile = -1). */
 wdlb_status wdlb_tile_info(const wdlb_ctx *ctx, int32_t *tiled, int32_t *tile);
+
+/* How the context's tiled shell kernel stages its field tile: *tma 1 if
+ * bricks whose tile needs no periodic wrap load it as one TMA box per array
+ * (sigma 4, FP32/FP16 storage, nx a multiple of 4, staging WDLB_STAGING_AUTO),
+ * 0 if every brick copies it node by node.  No counterpart in the paper. */
+wdlb_status wdlb_staging_info(const wdlb_ctx *ctx, int32_t *tma);
 
 /* Forget every autotuned entry (later contexts probe again). */
 void wdlb_autotune_reset(void);

@@ -3,6 +3,8 @@
 // reductions and host transfers.  All arithmetic of the method runs in the
 // kernels of wdlb_kernels.cuh; this file only validates, lays out memory and
 // enqueues work on the context stream.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +58,7 @@ struct Tables {
 struct Layout {
     size_t f[2], nu, hb, cprev, tprev, nscale, stage, snap, partial, result, status, shell_e, shell_k, ball;
     size_t params, kbufs, items;   // one-slot step tables (KParams, KBufs of both parities, work items)
+    size_t tmaps;                  // tensor maps of the TMA tile (nu, hb), 64-byte aligned
     size_t nitems;
     size_t total;
 };
@@ -101,8 +104,50 @@ Layout layout_for(wdlb_lattice lat, long long N, long long Npad, int storage, in
     L.kbufs = take(2 * kKBufsMaxBytes);
     L.nitems = step_items(lat, N);
     L.items = take(L.nitems * sizeof(BatchItem));
+    L.tmaps = take(2 * sizeof(CUtensorMap));
     L.total = off;
     return L;
+}
+
+// cuTensorMapEncodeTiled of the driver, through the runtime's entry-point
+// query (no link against the driver library); NULL if unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor maps of the tiled shell kernel's TMA staging (sigma 4: halo 4, tile
+// 16 x 16 x (TZ + 8) nodes): nu as the 4-D tensor (component, x, y, z) of
+// floats, hb as the 3-D tensor (x, y, z).  Needs 16-byte row strides for hb
+// (nx a multiple of 4).  Returns false where the kernel must stage per node.
+bool encode_tile_maps(const KParams &p, const wdlb_options &o, void *nu, void *hb, CUtensorMap maps[2])
+{
+    if (!p.tiled || p.s2 != 8 || o.storage == WDLB_STORE_F64 || o.staging != WDLB_STAGING_AUTO) return false;
+    if (p.nx % 4 != 0 || p.nx < 16 || p.ny < 16) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint32_t SZ = (cuuint32_t)(tile_depth(p.tile) + 8);
+    const cuuint64_t nx = p.nx, ny = p.ny, nz = p.nz;
+    const cuuint64_t dnu[4] = {4, nx, ny, nz}, snu[3] = {16, 16 * nx, 16 * nx * ny};
+    const cuuint32_t bnu[4] = {4, 16, 16, SZ}, es[4] = {1, 1, 1, 1};
+    const cuuint64_t dhb[3] = {nx, ny, nz}, shb[2] = {4 * nx, 4 * nx * ny};
+    const cuuint32_t bhb[3] = {16, 16, SZ};
+    return enc(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, nu, dnu, snu, bnu, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+           enc(&maps[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, hb, dhb, shb, bhb, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 const Launchers &launchers_for(int storage)
@@ -201,6 +246,8 @@ wdlb_status check_status_word(wdlb_ctx *ctx)
     WDLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (h & kStatusBounds)
         return fail(ctx, WDLB_ERR_CUDA, "checked build: a kernel index left its array (the access was skipped)");
+    if (h & kStatusTimeout)
+        return fail(ctx, WDLB_ERR_TIMEOUT, "a bounded wait for the TMA tile ran out (the brick was skipped)");
     if (h) return fail(ctx, WDLB_ERR_UNSTABLE, "non-physical state: smeared packing fraction >= 1 or density not finite/positive");
     return WDLB_OK;
 }
@@ -618,6 +665,10 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
     ctx->dev.shell_e = reinterpret_cast<const int4 *>(b + L.shell_e);
     ctx->dev.shell_k = b + L.shell_k;
     ctx->dev.ball = reinterpret_cast<const int4 *>(b + L.ball);
+    ctx->kp.wait_limit = o.wait_limit != 0 ? o.wait_limit : kDefaultWaitLimit;
+    CUtensorMap maps[2];
+    ctx->kp.tma = encode_tile_maps(ctx->kp, o, ctx->dev.nu, ctx->dev.hb, maps) ? 1 : 0;
+    ctx->kp.tmaps = ctx->kp.tma ? b + L.tmaps : nullptr;
 
     // tables to the device
     std::vector<int4> se(std::max(nshell, 1)), be(std::max(nball, 1));
@@ -644,6 +695,8 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b + L.ball, be.data(), be.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev.status, 0, 16 * sizeof(int), ctx->stream);
+    if (e == cudaSuccess && ctx->kp.tma)
+        e = cudaMemcpyAsync(b + L.tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = upload_step_tables(ctx);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
@@ -1020,6 +1073,13 @@ wdlb_status wdlb_tile_info(const wdlb_ctx *ctx, int32_t *tiled, int32_t *tile)
     if (!ctx) return WDLB_ERR_ARG;
     if (tiled) *tiled = ctx->kp.tiled;
     if (tile) *tile = ctx->kp.tiled ? ctx->kp.tile : -1;
+    return WDLB_OK;
+}
+
+wdlb_status wdlb_staging_info(const wdlb_ctx *ctx, int32_t *tma)
+{
+    if (!ctx || !tma) return WDLB_ERR_ARG;
+    *tma = ctx->kp.tiled ? ctx->kp.tma : 0;
     return WDLB_OK;
 }
 
@@ -1537,7 +1597,10 @@ wdlb_status wdlb_batch_residuals(wdlb_batch *b, int32_t interval, double *res, i
         }
         if (res) res[s] = v;
         if (status)
-            status[s] = c ? ((stw[s] & kStatusBounds) ? WDLB_ERR_CUDA : (stw[s] ? WDLB_ERR_UNSTABLE : WDLB_OK)) : -1;
+            status[s] = c ? ((stw[s] & kStatusBounds)    ? WDLB_ERR_CUDA
+                             : (stw[s] & kStatusTimeout) ? WDLB_ERR_TIMEOUT
+                             : (stw[s] ? WDLB_ERR_UNSTABLE : WDLB_OK))
+                          : -1;
     }
     return WDLB_OK;
 }

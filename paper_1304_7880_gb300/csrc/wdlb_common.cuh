@@ -55,6 +55,9 @@ struct KParams {
     int ball_tiled;          // 1: use the shared-memory tiled ball sum
     int shell_rule;          // 0: full shell, uniform weight wshell; 1: compact shell,
                              // per-vector weights in shell_k[m].w (wshell = 1)
+    int tma;                 // 1: the tiled shell kernel stages interior bricks' tiles by TMA
+    int wait_limit;          // polls of an mbarrier wait before it gives up (status bit 4)
+    const void *tmaps;       // device tensor maps of nu and hb for the TMA tile (64-byte aligned)
     double g[3];             // external acceleration
     double omega;            // 1/tau
     double tau;
@@ -111,6 +114,8 @@ struct KBufs {
 #endif
 constexpr int kStatusUnstable = 1;   // status word bits
 constexpr int kStatusBounds = 2;
+constexpr int kStatusTimeout = 4;    // a bounded wait (TMA tile) gave up
+constexpr int kDefaultWaitLimit = 1 << 22;   // mbarrier polls, each followed by a short sleep
 
 __device__ __forceinline__ bool in_bounds(long long i, long long n, int *status)
 {
@@ -136,6 +141,63 @@ __device__ __forceinline__ void cp_async_ca(void *smem, const void *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// TMA (cp.async.bulk.tensor) with an mbarrier in shared memory that counts
+// the bytes the copies deliver.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the asynchronous (TMA) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Poll the barrier's phase 0 at most `limit` times; true once it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, int limit)
+{
+    for (int it = 0; it < limit; it++) {
+        if (mbar_test_wait(bar, 0)) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+// Tiled loads of a 3-D / 4-D box of a tensor map into shared memory (the
+// innermost coordinate first; coordinates outside the tensor read zero).
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int c0, int c1, int c2, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
 
 // Contact value of the homogeneous hard-sphere pair distribution at packing
 // fraction chi (closure 0: Carnahan-Starling, 1: Percus-Yevick, 2: one).

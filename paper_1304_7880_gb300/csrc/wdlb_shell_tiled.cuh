@@ -219,8 +219,18 @@ constexpr size_t smem_bytes()
 {
     constexpr int R = shell_radius(S2);
     constexpr size_t n = size_t(TX + 2 * R) * (TY + 2 * R) * (tz_of(V) + 2 * R);
-    return n * (sizeof(float4) + sizeof(float)) +
-           size_t(shell_count(S2) / 2) * (sizeof(float4) + (WT ? sizeof(float) : 0));
+    const size_t tables = size_t(shell_count(S2) / 2) * (sizeof(float4) + (WT ? sizeof(float) : 0));
+    return n * (sizeof(float4) + sizeof(float)) + (tables + 7) / 8 * 8 + sizeof(uint64_t);   // + the mbarrier
+}
+
+// TMA staging of the tile: for a halo R that is a multiple of 4 (sigma 4),
+// the tile's first x coordinate x0 - R is a multiple of 4 floats (16 bytes),
+// so the nu tile is one box (4 floats x 16 x 16 x (TZ + 2R) nodes) of the 4-D
+// tensor (component, x, y, z) and the hb tile one box of the 3-D tensor.
+template <int S2>
+constexpr bool tma_staging()
+{
+    return shell_radius(S2) % 4 == 0 && TX + 2 * shell_radius(S2) <= 256;
 }
 
 // Blocks per SM the launch bounds ask for: for 256 threads, three where three
@@ -247,11 +257,16 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
     constexpr int NPAIR = shell_count(S2) / 2;
     constexpr int NT = threads_of(V);
     constexpr int ZSTEP = NT / (TX * TY);     // z rows covered by one pass of the block
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // shared memory: nu tile (16 B per node), hb tile (4 B per node), pair
+    // table, pair weights, mbarrier; the two tiles 128-byte aligned for TMA
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *sm4 = reinterpret_cast<float4 *>(smem_raw);
-    float4 *smt = reinterpret_cast<float4 *>(smem_raw + sizeof(float4) * NS);
-    float *smh = reinterpret_cast<float *>(smem_raw + sizeof(float4) * (NS + NPAIR));
-    float *smw = smh + NS;                    // pair weights (WT)
+    float *smh = reinterpret_cast<float *>(smem_raw + sizeof(float4) * NS);
+    float4 *smt = reinterpret_cast<float4 *>(smem_raw + (sizeof(float4) + sizeof(float)) * NS);
+    float *smw = reinterpret_cast<float *>(smt + NPAIR);   // pair weights (WT)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(
+        smem_raw + smem_bytes<S2, V, WT>() - sizeof(uint64_t));
+    static_assert(((sizeof(float4) + sizeof(float)) * NS) % 16 == 0, "pair table alignment");
     const int npair = WT ? (p.nshell >> 1) : NPAIR;
     constexpr bool CT = ct::compiled<S2, WT>();
 
@@ -276,9 +291,50 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
             wo[decltype(O)::value] = b.shell_k[2 * m].w;
         });
     }
-    // the field tile with its halo
+    // the field tile with its halo: one TMA box per array where the tile needs
+    // no periodic wrap in x and y (and z without walls), else per-node copies
     const float noff = float(p.n_off), hoff = float(p.h_off);
-    for (int idx = threadIdx.x; idx < NS; idx += NT) {
+    bool use_tma = false;
+    if constexpr (tma_staging<S2>()) {
+        // (TMA writes shared memory at 128-byte aligned addresses only)
+        use_tma = p.tma && (smem_u32(sm4) & 127u) == 0 && x0 - R >= 0 && x0 + TX + R <= nx && y0 - R >= 0 &&
+                  y0 + TY + R <= ny && (WALLS || (z0 - R >= 0 && z0 + TZ + R <= nz));
+    }
+    if (use_tma) {
+        // wait_limit < 0 (tests only): no copy is issued and the barrier is
+        // never completed, so the wait runs out after -wait_limit polls
+        const bool probe = p.wait_limit < 0;
+        const int limit = probe ? -p.wait_limit : p.wait_limit;
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            if (!probe) {
+                mbar_arrive_expect_tx(bar, (unsigned)(NS * (sizeof(float4) + sizeof(float))));
+                const char *tm = static_cast<const char *>(p.tmaps);
+                tma_load_4d(sm4, tm, 0, x0 - R, y0 - R, z0 - R, bar);
+                tma_load_3d(smh, tm + 128, x0 - R, y0 - R, z0 - R, bar);
+            }
+        }
+        __syncthreads();   // the barrier is initialised before anyone polls it
+        const bool ok = mbar_wait_bounded(bar, limit);
+        if (__syncthreads_or(!ok)) {
+            // gave up: report it, then wait (bounded) for any copy in flight
+            // before the block's shared memory is released
+            if (threadIdx.x == 0) atomicOr(b.status, kStatusTimeout);
+            if (!probe) mbar_wait_bounded(bar, kDefaultWaitLimit);
+            return;
+        }
+        if (WALLS && (z0 - R < 0 || z0 + TZ + R > nz)) {
+            // the box read zeros beyond the lattice; beyond a wall n = 0
+            for (int idx = threadIdx.x; idx < NS; idx += NT) {
+                const int gz = z0 - R + idx / (SX * SY);
+                if (gz < 0 || gz >= nz) {
+                    sm4[idx] = make_float4(-noff, 0.f, 0.f, 0.f);
+                    smh[idx] = -hoff;
+                }
+            }
+        }
+    }
+    for (int idx = threadIdx.x; idx < (use_tma ? 0 : NS); idx += NT) {
         const int sx = idx % SX, sy = (idx / SX) % SY, sz = idx / (SX * SY);
         int gx = x0 - R + sx, gy = y0 - R + sy, gz = z0 - R + sz;
         gx = wrap_coord(gx, nx);
@@ -299,6 +355,7 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
     }
     cp_async_wait_all();
     __syncthreads();
+    if (use_tma && threadIdx.x == 0) mbar_inval(bar);
 
     const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, tzb = threadIdx.x >> 6;
 #pragma unroll 1

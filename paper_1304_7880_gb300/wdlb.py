@@ -45,7 +45,10 @@ class wdlb_options(ctypes.Structure):
                 ("interactions", ctypes.c_int32), ("k_cross", ctypes.c_double), ("n_ref", ctypes.c_double),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("tile", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("shell_rule", ctypes.c_int32)]
+                ("shell_rule", ctypes.c_int32), ("staging", ctypes.c_int32), ("wait_limit", ctypes.c_int32)]
+
+
+STAGINGS = {"auto": 0, "cp_async": 1}
 
 
 class wdlb_pore_desc(ctypes.Structure):
@@ -104,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "wdlb_profile_step": (I32, [P, I64, P]),
         "wdlb_fields_static": (I32, [wdlb_lattice, D, I32, I32, P, P, P, P, P, P]),
         "wdlb_launch_count": (I64, [P]),
+        "wdlb_staging_info": (I32, [P, P]),
         "wdlb_last_error": (ctypes.c_char_p, [P]),
         "wdlb_batch_create": (I32, [P, ctypes.c_uint64, I32, P]),
         "wdlb_batch_pore_bytes": (I32, [P, P, P]),
@@ -170,10 +174,12 @@ class Context:
 
 def wdlb_create(lattice, sigma, walls, tau, g=(0.0, 0.0, 0.0), closure="CS", omega_mode="const",
                 storage="f32", interactions=True, k_cross=2.0, n_ref=0.0, device=None, tile=-1, autotune=True,
-                shell_rule="full"):
+                shell_rule="full", staging="auto", wait_limit=0):
     """Create a context; device memory and stream come from PyTorch.  tile: -1
     (autotuner) or a forced tile shape 0, 1, 2 of the tiled shell kernel;
-    shell_rule: "full" or "compact" contact-shell quadrature."""
+    shell_rule: "full" or "compact" contact-shell quadrature; staging: "auto"
+    (TMA tiles where possible) or "cp_async"; wait_limit: polls of the TMA
+    tile's wait (0: the library's default)."""
     import torch
 
     lib = load_library()
@@ -190,6 +196,8 @@ def wdlb_create(lattice, sigma, walls, tau, g=(0.0, 0.0, 0.0), closure="CS", ome
     opt.tile = int(tile)
     opt.autotune = 1 if autotune else 0
     opt.shell_rule = SHELL_RULES[shell_rule]
+    opt.staging = STAGINGS[staging]
+    opt.wait_limit = int(wait_limit)
     walls_i = 1 if walls else 0
     nbytes = ctypes.c_uint64()
     _check(lib.wdlb_workspace_size(lat, float(sigma), walls_i, ctypes.byref(opt), ctypes.byref(nbytes)))
@@ -310,6 +318,13 @@ def wdlb_tile_info(ctx: Context):
     tiled, tile = ctypes.c_int32(), ctypes.c_int32()
     _check(load_library().wdlb_tile_info(ctx.handle, ctypes.byref(tiled), ctypes.byref(tile)), ctx)
     return bool(tiled.value), tile.value
+
+
+def wdlb_staging_info(ctx: Context) -> bool:
+    """True if the context's tiled shell kernel loads interior tiles by TMA."""
+    tma = ctypes.c_int32()
+    _check(load_library().wdlb_staging_info(ctx.handle, ctypes.byref(tma)), ctx)
+    return bool(tma.value)
 
 
 def wdlb_autotune_reset():
