@@ -71,8 +71,12 @@ enum { WDLB_CLOSURE_CS = 0, WDLB_CLOSURE_PY = 1, WDLB_CLOSURE_ONE = 2 };
  * clamped to tau >= 0.501. */
 enum { WDLB_OMEGA_CONST = 0, WDLB_OMEGA_NBAR = 1 };
 /* Population storage: plain FP64 (FP64 arithmetic), FP32 deviation from the
- * rest state w_q n_ref (FP32 arithmetic), FP16 relative deviation
- * f_q / (w_q n_ref) - 1 (FP32 arithmetic). */
+ * node's rest state w_q s(r) (FP32 arithmetic), FP16 relative deviation
+ * f_q / (w_q s(r)) - 1 (FP32 arithmetic).  FP16 is accepted for periodic boxes
+ * only (WDLB_WALLS_NONE; with walls wdlb_create, wdlb_workspace_size and
+ * wdlb_batch_add return WDLB_ERR_ARG): in a driven slit its 10-bit deviations
+ * leave steady-state u_x errors of 2 to 15 %, and it is no faster than FP32,
+ * whose step is bound by arithmetic, not by HBM. */
 enum { WDLB_STORE_F64 = 0, WDLB_STORE_F32 = 1, WDLB_STORE_F16 = 2 };
 /* Quadrature of the integral over khat in Eq. campoc (the paper leaves the
  * discrete form open):

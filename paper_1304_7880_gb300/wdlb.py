@@ -466,7 +466,7 @@ def _bcheck(status, batch=None):
 
 
 def wdlb_batch_create(max_pores, pool_bytes, closure="CS", omega_mode="const", storage="f32", interactions=True,
-                      k_cross=2.0, device=None, shell_rule="full"):
+                      k_cross=2.0, device=None, shell_rule="full", autotune=True, staging="auto"):
     import torch
 
     lib = load_library()
@@ -478,6 +478,8 @@ def wdlb_batch_create(max_pores, pool_bytes, closure="CS", omega_mode="const", s
     opt.interactions = 1 if interactions else 0
     opt.k_cross = float(k_cross)
     opt.shell_rule = SHELL_RULES[shell_rule]
+    opt.autotune = 1 if autotune else 0
+    opt.staging = STAGINGS[staging]
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     pool = torch.empty(int(pool_bytes) + 256, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)

@@ -24,7 +24,7 @@ CASES = {
     "s6_slit_compact_t%d": ((12, 9, 35), 6.0, True, "f32", "compact"),
 }
 SINGLE = {
-    "s4_slit_f16": ((10, 8, 27), 4.0, True, "f16", "full"),
+    "s4_bulk_f16": ((12, 8, 27), 4.0, False, "f16", "full"),
     "s4_slit_f64": ((10, 8, 27), 4.0, True, "f64", "full"),
     "s3.5_slit_compact": ((11, 9, 15), 3.5, True, "f32", "compact"),
     "s8_bulk_compact": ((16, 16, 20), 8.0, False, "f32", "compact"),

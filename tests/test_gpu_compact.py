@@ -4,8 +4,8 @@ keeps the virial coefficient, the long-wave shear viscosity and a fourth-rank
 isotropic moment) against the FP64 oracle running the same rule.
 
 Tolerances are those of the full shell (test_gpu_parity): FP64 1e-10, FP32
-1e-5 on n and u in bulk boxes, FP16 n 1e-6 / u 5e-3 (bulk) and n 1e-3 / u 0.2
-(walls).  Batches with the compact rule step bit-identically alone and
+1e-5 on n and u in bulk boxes, FP16 n 1e-6 / u 5e-3 (bulk; FP16 is refused
+in slits).  Batches with the compact rule step bit-identically alone and
 batched.
 """
 import math
@@ -18,7 +18,6 @@ from paper_1304_7880_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": (1e-10, 1e-10), "f32": (1e-5, 1e-5), "f16": (1e-6, 5e-3)}
-TOL_WALLS = {"f64": (1e-10, 1e-10), "f32": (1e-5, 1e-5), "f16": (1e-3, 0.2)}
 
 
 @pytest.fixture(scope="module")
@@ -111,11 +110,13 @@ def test_compact_tiled_fp32_ragged(w, oracle_mod, name, tile):
 @pytest.mark.parametrize("name", sorted(TILED))
 def test_compact_tiled_fp16_ragged(w, oracle_mod, name):
     p = TILED[name]
+    if p["walls"]:
+        pytest.skip("FP16 storage is for periodic boxes only")
     n, u = noisy_state(p, 0.4, 2e-2, 17)
     ctx, o = make_pair(w, oracle_mod, p, n, u, "f16")
     w.wdlb_step(ctx, 20)
     o.step(20)
-    compare(ctx, o, p["walls"], TOL_WALLS["f16"] if p["walls"] else TOL["f16"], w)
+    compare(ctx, o, p["walls"], TOL["f16"], w)
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])

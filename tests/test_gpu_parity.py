@@ -11,7 +11,7 @@ Tolerances (stated per storage and workload):
   ~eps * 0.1 w n per step; the measured floor is 2.4e-4 of max|u_x| after
   1000 steps (n 1.5e-7, mean density 6e-8).
   FP16 relative-deviation storage (10-bit mantissa): bulk n 1e-6, u 5e-3 of
-  max|u|; driven slit n 1e-3, u 0.2 of max|u_x|, flux 0.1.
+  max|u|; refused in slits (steady-state u_x errors of 2 to 15 %).
 """
 import math
 
@@ -23,7 +23,7 @@ from paper_1304_7880_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": (1e-10, 1e-10), "f32": (1e-5, 1e-5), "f16": (1e-6, 5e-3)}
-TOL_SLIT = {"f32": (1e-6, 5e-4, 5e-4), "f16": (1e-3, 0.2, 0.1)}
+TOL_SLIT = {"f32": (1e-6, 5e-4, 5e-4)}
 
 
 @pytest.fixture(scope="module")
@@ -106,7 +106,21 @@ def test_slit_8x8x41_f64(w, oracle_mod):
         compare(ctx, o, True, "f64", w)
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_fp16_storage_refused_in_slits(w):
+    """FP16 storage is for periodic boxes: with walls the library refuses it
+    (its steady-state u_x errors in slits are 2 to 15 %)."""
+    with pytest.raises(w.WDLBError) as ei:
+        w.wdlb_create((8, 8, 41), 4.0, True, 1.0, (1e-6, 0, 0), storage="f16")
+    assert ei.value.status == 1
+    b = w.wdlb_batch_create(2, 64 << 20, storage="f16")
+    p, n, u = synth.slit_8x8x41()
+    with pytest.raises(w.WDLBError) as ei:
+        w.wdlb_batch_add(b, (8, 8, 41), 4.0, True, 1.0, p["g"], n, u)
+    assert ei.value.status == 1
+    w.wdlb_batch_destroy(b)
+
+
+@pytest.mark.parametrize("storage", ["f32"])
 def test_slit_8x8x41_reduced_precision(w, oracle_mod, storage):
     """The plain slit workload, 1000 steps, against the FP64 oracle (stated
     slit bounds in the module docstring)."""
@@ -183,13 +197,14 @@ def test_tiled_fp16_ragged(w, oracle_mod, name):
     deviations) on the ragged cases, in the autotuner's shape, within the FP16
     bounds (bulk n 1e-6, u 5e-3; walls n 1e-3, u 0.2)."""
     p = TILED_CASES[name]
+    if p["walls"]:
+        pytest.skip("FP16 storage is for periodic boxes only")
     n, u = random_state((p["nz"], p["ny"], p["nx"]), p["sigma"], 0.4, 2e-2, 17, p["walls"])
     ctx, o = make_pair(w, oracle_mod, p, n, u, "f16")
     assert w.wdlb_tile_info(ctx)[0]
     w.wdlb_step(ctx, 20)
     o.step(20)
-    tol = TOL_SLIT["f16"][:2] if p["walls"] else TOL["f16"]
-    compare(ctx, o, p["walls"], "f16", w, tol=tol)
+    compare(ctx, o, p["walls"], "f16", w, tol=TOL["f16"])
 
 
 def test_autotuner_records_and_applies_its_choice(w):

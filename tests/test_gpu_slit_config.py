@@ -3,8 +3,10 @@ tau = 0.8, g_x = 1e-6) on the GPU.
 
 * Steady state against the FP64 oracle (tests/golden/slit_column_steady.txt,
   written by make_slit_column_steady.py from the oracle alone), per quantity:
-  density profile n(z), velocity profile u_x(z) and pore flux, for FP32 and
-  FP16 population storage, both converged (three times the oracle's steps).  A uniform start stays uniform in x and y, so an
+  density profile n(z), velocity profile u_x(z) and pore flux, for FP32
+  population storage, converged (three times the oracle's steps); FP16
+  storage, refused in slits by the library, measured 2 to 15 % in u_x here
+  before that.  A uniform start stays uniform in x and y, so an
   8 x 8 cross-section (the smallest the tiled kernel takes) solves the same
   discrete problem as 256 x 256.
 * The full 256 x 256 x 161 lattice in the tiled launch configuration stays
@@ -19,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "slit_column_steady.txt")
 NZ, SIGMA, TAU, GX = 161, 4.0, 0.8, 1e-6
-# Both storages run three times the oracle's step count, which converges them
+# The runs take three times the oracle's step count, which converges them
 # down to their rounding noise (the FP32 pore flux then fluctuates by ~1e-9 to
 # 1e-8 per step): comparing at a 1e-8 or 1e-9 tolerance would measure
 # unfinished convergence (the slowest mode relaxes over ~1.7e4 steps) rather
@@ -27,9 +29,9 @@ NZ, SIGMA, TAU, GX = 161, 4.0, 0.8, 1e-6
 STEP_FACTOR = 3
 # Per-quantity bounds against the oracle: (n relative, u_x / max|u_x|, flux
 # relative).  Measured (converged): FP32 n 1.4e-7 / 4.2e-7, u_x 1.0e-5 /
-# 3.2e-5, flux 1.1e-5 / 1.5e-5 (n* 0.3 / 0.6); FP16 n 2.0e-4 / 6.9e-5, u_x
-# 0.155 / 0.017, flux 0.14 / 0.005.
-BOUNDS = {"f32": (1e-6, 5e-5, 3e-5), "f16": (5e-4, 0.2, 0.2)}
+# 3.2e-5, flux 1.1e-5 / 1.5e-5 (n* 0.3 / 0.6).  (FP16, before the library
+# refused it in slits: n 2.0e-4 / 6.9e-5, u_x 0.155 / 0.017, flux 0.14 / 0.005.)
+BOUNDS = {"f32": (1e-6, 5e-5, 3e-5)}
 
 
 @pytest.fixture(scope="module")
@@ -65,7 +67,7 @@ def uniform_slit(nxy, n_star):
     return n
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32"])
 @pytest.mark.parametrize("n_star", [0.3, 0.6])
 def test_steady_slit_against_oracle(w, storage, n_star):
     ref = golden()[n_star]
