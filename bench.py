@@ -446,6 +446,32 @@ def run_reference(args):
     return 0
 
 
+def run_box_only(args, w, synth, torch):
+    """The 128^3 bulk box alone, device-resident (for profiling): warm-up, then
+    `steps` benchmark steps of SUB time steps, and one instrumented pass."""
+    p, n, u = synth.bulk_shear_128(sigma=SIGMA)
+    ctx = w.wdlb_create((L, L, L), p["sigma"], False, p["tau"], p["g"], storage="f32", tile=args.tile,
+                        shell_rule=args.shell_rule)
+    w.wdlb_init_fields_device(ctx, torch.from_numpy(n).cuda(), torch.from_numpy(u).cuda())
+    for _ in range(args.warmup):
+        w.wdlb_step(ctx, SUB)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(ctx.stream)
+    for _ in range(args.steps):
+        w.wdlb_step(ctx, SUB)
+    b.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = w.wdlb_profile_step(ctx, SUB)
+    print(json.dumps({"only_device": True, "workload": WORKLOAD, "shell_rule": args.shell_rule,
+                      "value": L ** 3 * SUB * args.steps / (a.elapsed_time(b) * 1e-3) / 1e6, "unit": UNIT,
+                      "kernels_ms": ms, "tile_shape": w.wdlb_tile_info(ctx)[1], "tma": w.wdlb_staging_info(ctx)}),
+          flush=True)
+    w.wdlb_destroy(ctx)
+    return 0
+
+
 def fp32_peak_tflops(sm_count, sm_mhz):
     """FP32 FMA issue peak: SMs x 128 lanes x 2 flops x clock."""
     return sm_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
@@ -471,6 +497,9 @@ def run_ours(args):
         build.build()
     barrier()
     from paper_1304_7880_gb300 import wdlb as w
+
+    if args.only_device and args.workload == "bulk128":
+        return run_box_only(args, w, synth, torch)
 
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
@@ -774,6 +803,8 @@ def main():
     ap.add_argument("--only-device", action="store_true",
                     help="time only the device-resident loop (for profiling); no e2e, baseline or other paths")
     ap.add_argument("--sub", type=int, default=SUB, help="lattice time steps per benchmark step")
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "bulk128"],
+                    help="with --only-device: the 64-pore batch (default) or the 128^3 bulk box")
     ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="tile shape of the tiled shell kernel (-1: autotuner)")
     args = ap.parse_args()
