@@ -451,7 +451,7 @@ def run_box_only(args, w, synth, torch):
     `steps` benchmark steps of SUB time steps, and one instrumented pass."""
     p, n, u = synth.bulk_shear_128(sigma=SIGMA)
     ctx = w.wdlb_create((L, L, L), p["sigma"], False, p["tau"], p["g"], storage="f32", tile=args.tile,
-                        shell_rule=args.shell_rule)
+                        shell_rule=args.shell_rule, interactions=bool(args.interactions))
     w.wdlb_init_fields_device(ctx, torch.from_numpy(n).cuda(), torch.from_numpy(u).cuda())
     for _ in range(args.warmup):
         w.wdlb_step(ctx, SUB)
@@ -805,6 +805,8 @@ def main():
     ap.add_argument("--sub", type=int, default=SUB, help="lattice time steps per benchmark step")
     ap.add_argument("--workload", default="batch64", choices=["batch64", "bulk128"],
                     help="with --only-device: the 64-pore batch (default) or the 128^3 bulk box")
+    ap.add_argument("--interactions", type=int, default=1, choices=[0, 1],
+                    help="with --workload bulk128: 0 skips the shell sums (profiling the per-node work alone)")
     ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="tile shape of the tiled shell kernel (-1: autotuner)")
     args = ap.parse_args()

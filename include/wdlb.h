@@ -132,8 +132,9 @@ typedef struct {
                                  Both give bitwise the same tile                     */
     int32_t wait_limit;       /* polls of the TMA tile's wait before the kernel gives
                                  up, reports WDLB_ERR_TIMEOUT and skips the brick
-                                 (0: the default, ~4 million polls with short
-                                 sleeps).  Negative values are for tests of that
+                                 (0: the default, about a million tries, each of
+                                 which may suspend the thread briefly in
+                                 hardware).  Negative values are for tests of that
                                  path: the kernel then issues no copy and waits on
                                  a barrier that nothing completes, for -wait_limit
                                  polls; the step's results are then not meaningful */

@@ -115,7 +115,7 @@ struct KBufs {
 constexpr int kStatusUnstable = 1;   // status word bits
 constexpr int kStatusBounds = 2;
 constexpr int kStatusTimeout = 4;    // a bounded wait (TMA tile) gave up
-constexpr int kDefaultWaitLimit = 1 << 22;   // mbarrier polls, each followed by a short sleep
+constexpr int kDefaultWaitLimit = 1 << 20;   // mbarrier try_wait calls (each suspends briefly)
 
 __device__ __forceinline__ bool in_bounds(long long i, long long n, int *status)
 {
@@ -156,11 +156,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned by
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity)
+// One potentially blocking test of the barrier's phase: the hardware may
+// suspend the thread until the phase completes or a short time limit passes.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
 {
     unsigned ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
@@ -170,13 +172,11 @@ __device__ __forceinline__ void mbar_inval(uint64_t *bar)
 {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// Poll the barrier's phase 0 at most `limit` times; true once it completed.
+// Wait for the barrier's phase 0 with at most `limit` tries; true once it completed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, int limit)
 {
-    for (int it = 0; it < limit; it++) {
-        if (mbar_test_wait(bar, 0)) return true;
-        __nanosleep(32);
-    }
+    for (int it = 0; it < limit; it++)
+        if (mbar_try_wait(bar, 0)) return true;
     return false;
 }
 // Tiled loads of a 3-D / 4-D box of a tensor map into shared memory (the
