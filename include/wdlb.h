@@ -138,6 +138,14 @@ typedef struct {
                                  path: the kernel then issues no copy and waits on
                                  a barrier that nothing completes, for -wait_limit
                                  polls; the step's results are then not meaningful */
+    int32_t persistent;       /* batches: 0 (default) one launch per phase (moments,
+                                 smeared density, shell) for all pores, replayed from
+                                 CUDA graphs; 1 one persistent kernel per
+                                 wdlb_batch_step call in which each pore's phases
+                                 follow one another without device-wide barriers
+                                 (used where every pore runs the tiled sigma-4 kernel
+                                 on 8 x 8 x 4 bricks, else the default).  Both give
+                                 bitwise the same results                            */
 } wdlb_options;
 enum { WDLB_STAGING_AUTO = 0, WDLB_STAGING_CP_ASYNC = 1 };
 

@@ -1139,6 +1139,8 @@ struct wdlb_batch {
     std::vector<Slot> slots;
     // device tables
     KParams *d_params = nullptr;
+    int *d_flow = nullptr;             // persistent step: counts [3P], done [3P], next, abort
+    bool flow = false;                 // the persistent kernel serves the current tables
     char *d_bufs[2] = {nullptr, nullptr};
     BatchItem *d_items = nullptr;
     size_t items_cap = 0;
@@ -1297,7 +1299,17 @@ wdlb_status batch_build(wdlb_batch *b)
         all.insert(all.end(), g.second.begin(), g.second.end());
     }
     cudaError_t e = cudaSuccess;
-    if (P > 0) e = cudaMemcpyAsync(b->d_params, params.data(), P * sizeof(KParams), cudaMemcpyHostToDevice, b->stream);
+    // item counts per slot and phase for the persistent step
+    b->flow = b->opt.persistent && b->L->flow_ok(L);
+    std::vector<int> counts(3 * size_t(std::max(P, 1)), 0);
+    for (const BatchItem &it : node_items) counts[3 * it.slot + 0]++;
+    for (const BatchItem &it : ball_items) counts[3 * it.slot + 1]++;
+    for (auto &g : groups)
+        for (const BatchItem &it : g.second) counts[3 * it.slot + 2]++;
+    if (P > 0 && b->flow)
+        e = cudaMemcpyAsync(b->d_flow, counts.data(), 3 * P * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && P > 0)
+        e = cudaMemcpyAsync(b->d_params, params.data(), P * sizeof(KParams), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && P > 0)
         e = cudaMemcpyAsync(b->d_bufs[0], bufs0.data(), bufs0.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && P > 0)
@@ -1428,7 +1440,8 @@ wdlb_status wdlb_batch_create(const wdlb_options *opt, uint64_t pool_bytes, int3
     }
     b->pool_bytes = pool_bytes & ~size_t(255);
     b->free_list.push_back(std::make_pair(size_t(0), b->pool_bytes));
-    if (cudaMalloc(&b->d_params, max_pores * sizeof(KParams)) != cudaSuccess ||
+    if (cudaMalloc(&b->d_flow, (6 * size_t(max_pores) + 8) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_params, max_pores * sizeof(KParams)) != cudaSuccess ||
         cudaMalloc(&b->d_bufs[0], max_pores * b->L->kbufs_bytes) != cudaSuccess ||
         cudaMalloc(&b->d_bufs[1], max_pores * b->L->kbufs_bytes) != cudaSuccess) {
         wdlb_batch_destroy(b);
@@ -1504,6 +1517,29 @@ wdlb_status wdlb_batch_step(wdlb_batch *b, int64_t nsteps)
     if (b->dirty) {
         wdlb_status s = batch_build(b);
         if (s != WDLB_OK) return s;
+    }
+    if (b->flow && nsteps > 0) {
+        // one persistent launch for all nsteps (counters zeroed first)
+        const int P = (int)b->slots.size();
+        FlowLaunch F;
+        F.count = b->d_flow;
+        F.done = b->d_flow + 3 * P;
+        F.next = reinterpret_cast<unsigned *>(b->d_flow + 6 * P);
+        F.abort_flag = b->d_flow + 6 * P + 1;
+        F.nsteps = (int)nsteps;
+        F.parity0 = (int)(b->steps_since_build & 1);
+        F.nslots = P;
+        F.wait_limit = b->opt.wait_limit != 0 ? b->opt.wait_limit : kDefaultWaitLimit;
+        cudaError_t e = cudaMemsetAsync(F.done, 0, (3 * P + 2) * sizeof(int), b->stream);
+        if (e == cudaSuccess) e = b->L->flow_step(b->launch, F, b->stream, &b->launches);
+        if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "persistent batch step: %s", cudaGetErrorString(e));
+        b->steps_since_build += nsteps;
+        for (auto &sl : b->slots)
+            if (sl.ctx) {
+                sl.ctx->cur ^= (int)(nsteps & 1);
+                sl.ctx->steps += nsteps;
+            }
+        return WDLB_OK;
     }
     int64_t left = nsteps;
     if (b->steps_since_build & 1) {
@@ -1643,6 +1679,7 @@ void wdlb_batch_destroy(wdlb_batch *b)
         if (s.ctx) wdlb_destroy(s.ctx);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_params) cudaFree(b->d_params);
+    if (b->d_flow) cudaFree(b->d_flow);
     for (auto &p : b->d_bufs)
         if (p) cudaFree(p);
     if (b->owns_pool && b->pool) cudaFree(b->pool);

@@ -6,6 +6,7 @@
 #include "wdlb_step_kernels.cuh"
 #include "wdlb_tables.h"
 
+#include <algorithm>
 #include <cstring>
 
 #ifndef WDLB_STORAGE
@@ -298,9 +299,76 @@ cudaError_t do_batch_step(const BatchLaunch &L, int parity, int part, int group,
     return cudaGetLastError();
 }
 
+bool do_flow_ok(const BatchLaunch &L)
+{
+#if WDLB_STORAGE != 0
+    if (L.n_ball_node_items != 0 || L.ngroups != 1 || L.n_ball_items == 0) return false;
+    const BatchGroup &G = L.groups[0];
+    return G.tiled && G.s2 == 8 && G.tile == 2 && G.closure == 0 && G.nitems > 0;
+#else
+    (void)L;
+    return false;
+#endif
+}
+
+#if WDLB_STORAGE != 0
+template <bool WALLS, bool WT>
+cudaError_t launch_flow(const BatchLaunch &L, const FlowLaunch &F, cudaStream_t st)
+{
+    auto kern = k_step_flow<S, 8, 2, WALLS, WT>;
+    const size_t smem = flow_smem_bytes<8, 2, WT>();
+    static int grid = 0;   // one per template instance: resident blocks on the whole GPU
+    if (grid == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0, sms = 0, per_sm = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+        if (e != cudaSuccess) return e;
+        grid = std::max(1, sms * per_sm);
+    }
+    FlowArgs a;
+    a.P = L.params;
+    a.B[0] = L.bufs[0];
+    a.B[1] = L.bufs[1];
+    a.items = L.node_items;   // moments, smeared-density and shell items are contiguous in the table
+    a.n0 = L.n_node_items;
+    a.n1 = L.n_ball_items;
+    a.n2 = L.groups[0].nitems;
+    a.nsteps = F.nsteps;
+    a.parity0 = F.parity0;
+    a.nslots = F.nslots;
+    a.count = F.count;
+    a.done = F.done;
+    a.next = F.next;
+    a.abort_flag = F.abort_flag;
+    a.wait_limit = F.wait_limit;
+    kern<<<grid, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+#endif
+
+cudaError_t do_flow_step(const BatchLaunch &L, const FlowLaunch &F, cudaStream_t st, int64_t *launches)
+{
+#if WDLB_STORAGE != 0
+    if (!do_flow_ok(L)) return cudaErrorInvalidValue;
+    const BatchGroup &G = L.groups[0];
+    cudaError_t e = G.walls ? (G.rule ? launch_flow<true, true>(L, F, st) : launch_flow<true, false>(L, F, st))
+                            : (G.rule ? launch_flow<false, true>(L, F, st) : launch_flow<false, false>(L, F, st));
+    *launches += 1;
+    return e;
+#else
+    (void)L;
+    (void)F;
+    (void)st;
+    (void)launches;
+    return cudaErrorInvalidValue;
+#endif
+}
+
 static_assert(sizeof(KBufs<S, T>) <= kKBufsMaxBytes, "KBufs larger than its table slot");
-const Launchers kL = {do_prepare, sizeof(KBufs<S, T>), kbufs_fill, do_batch_step, do_init,
-                      do_fields,  do_moments,         do_population, do_stats};
+const Launchers kL = {do_prepare,  sizeof(KBufs<S, T>), kbufs_fill,    do_batch_step, do_init,   do_fields,
+                      do_moments,  do_population,       do_stats,      do_flow_ok,    do_flow_step};
 
 }  // namespace
 

@@ -65,6 +65,17 @@ struct BatchLaunch {
 
 constexpr size_t kKBufsMaxBytes = 256;   // room for one KBufs of any storage type in a table
 
+// Persistent dataflow step of a batch (k_step_flow): per-slot item counts and
+// completion counters, the work counter and the abort flag in device memory
+// (done, next and abort_flag zeroed before each launch).
+struct FlowLaunch {
+    const int *count;    // [slot * 3 + phase]
+    int *done;           // [slot * 3 + phase]
+    unsigned *next;
+    int *abort_flag;
+    int nsteps, parity0, nslots, wait_limit;
+};
+
 struct Launchers {
     // per-context preparation outside any stream capture (kernel attributes);
     // returns whether the tiled shell kernel can serve these parameters
@@ -95,6 +106,11 @@ struct Launchers {
     // moments of buffer `cur`, then FP64 statistics into result[0..5] (see k_stats)
     cudaError_t (*stats)(const KParams &, const DevBufs &, int cur, int update_snap, cudaStream_t,
                          int64_t *launches);
+    // whether the persistent dataflow kernel serves these tables (one shell
+    // group: tiled sigma 4, 8 x 8 x 4 bricks; tiled smeared density for all),
+    // and its launch: F.nsteps time steps of every slot in one kernel
+    bool (*flow_ok)(const BatchLaunch &);
+    cudaError_t (*flow_step)(const BatchLaunch &, const FlowLaunch &F, cudaStream_t, int64_t *launches);
 };
 
 const Launchers &launchers_f64();

@@ -45,7 +45,8 @@ class wdlb_options(ctypes.Structure):
                 ("interactions", ctypes.c_int32), ("k_cross", ctypes.c_double), ("n_ref", ctypes.c_double),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("tile", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("shell_rule", ctypes.c_int32), ("staging", ctypes.c_int32), ("wait_limit", ctypes.c_int32)]
+                ("shell_rule", ctypes.c_int32), ("staging", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
+                ("persistent", ctypes.c_int32)]
 
 
 STAGINGS = {"auto": 0, "cp_async": 1}
@@ -466,7 +467,8 @@ def _bcheck(status, batch=None):
 
 
 def wdlb_batch_create(max_pores, pool_bytes, closure="CS", omega_mode="const", storage="f32", interactions=True,
-                      k_cross=2.0, device=None, shell_rule="full", autotune=True, staging="auto"):
+                      k_cross=2.0, device=None, shell_rule="full", autotune=True, staging="auto",
+                      persistent=False, wait_limit=0):
     import torch
 
     lib = load_library()
@@ -480,6 +482,8 @@ def wdlb_batch_create(max_pores, pool_bytes, closure="CS", omega_mode="const", s
     opt.shell_rule = SHELL_RULES[shell_rule]
     opt.autotune = 1 if autotune else 0
     opt.staging = STAGINGS[staging]
+    opt.persistent = 1 if persistent else 0
+    opt.wait_limit = int(wait_limit)
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     pool = torch.empty(int(pool_bytes) + 256, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
