@@ -624,8 +624,9 @@ def run_ours(args):
         for s in ss:
             w.wdlb_batch_remove(be, s)
 
-    e2e_steps = max(2, args.steps // 4)
-    e2e_step()
+    e2e_steps = max(4, args.steps // 2)
+    for _ in range(2):
+        e2e_step()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
