@@ -28,6 +28,7 @@ UNITS = [
     ("wdlb_api.o", "wdlb_api.cu", []),
     ("wdlb_launch_f64.o", "wdlb_launch.cu", ["-DWDLB_STORAGE=0"]),
     ("wdlb_launch_f32.o", "wdlb_launch.cu", ["-DWDLB_STORAGE=1"]),
+    ("wdlb_launch_f32dw.o", "wdlb_launch.cu", ["-DWDLB_STORAGE=1", "-DWDLB_DW_COLLISION=1"]),
     ("wdlb_launch_f16.o", "wdlb_launch.cu", ["-DWDLB_STORAGE=2"]),
     ("wdlb_static.o", "wdlb_static.cu", []),
 ]

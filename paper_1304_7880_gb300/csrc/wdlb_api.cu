@@ -22,6 +22,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/wdlb.h"
+#include "wdlb_dw.cuh"
 #include "wdlb_launch.h"
 #include "wdlb_tables.h"
 
@@ -150,10 +151,10 @@ bool encode_tile_maps(const KParams &p, const wdlb_options &o, void *nu, void *h
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-const Launchers &launchers_for(int storage)
+const Launchers &launchers_for(int storage, int collision)
 {
     if (storage == WDLB_STORE_F64) return launchers_f64();
-    if (storage == WDLB_STORE_F32) return launchers_f32();
+    if (storage == WDLB_STORE_F32) return collision == WDLB_COLLISION_DW ? launchers_f32dw() : launchers_f32();
     return launchers_f16();
 }
 
@@ -231,6 +232,10 @@ wdlb_status validate(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_o
         // deviations leave u_x errors of 2 to 15 % at steady state
         if (opt->storage == WDLB_STORE_F16 && walls == WDLB_WALLS_Z) return WDLB_ERR_ARG;
         if (!(opt->n_ref >= 0.0) || !std::isfinite(opt->k_cross)) return WDLB_ERR_ARG;
+        // the double-word collision: FP32 storage, lattices with walls
+        if (opt->collision < 0 || opt->collision > 1) return WDLB_ERR_ARG;
+        if (opt->collision == WDLB_COLLISION_DW && (opt->storage != WDLB_STORE_F32 || walls != WDLB_WALLS_Z))
+            return WDLB_ERR_ARG;
         if (opt->tile < -1 || opt->tile > 2 || opt->autotune < 0 || opt->autotune > 1) return WDLB_ERR_ARG;
         if (opt->shell_rule < 0 || opt->shell_rule > 1) return WDLB_ERR_ARG;
         if (opt->shell_rule == WDLB_SHELL_COMPACT) {
@@ -280,6 +285,9 @@ void set_params(wdlb_ctx *ctx)
     p.chi_of_n = M_PI * ctx->sigma * ctx->sigma * ctx->sigma / 6.0;
     p.c_half = p.chi_of_n / (2.0 * std::max(p.nball, 1));
     p.h_pred = KAPPA * p.beta / 6.0;
+    for (int d = 0; d < 3; d++) dw_split(p.g[d], p.g_dw[d]);
+    dw_split(p.omega, p.omega_dw);
+    dw_split(p.interactions ? p.k_cross * 4.5 : 0.0, p.ka_dw);
     const double s2 = 2.0 * ctx->sigma;
     p.s2 = (std::fabs(s2 - std::round(s2)) < 1e-12) ? (int)std::lround(s2) : 0;
     p.tiled = 0;
@@ -450,15 +458,16 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // Tile autotuner: a process-wide table (storage, 2 sigma, walls, nz, shell
-// rule) -> tile
+// rule, collision arithmetic) -> tile
 // shape of the tiled shell kernel, filled on first use by timing every shape
 // on a scratch lattice of the key, or from the built-in table.
 // ---------------------------------------------------------------------------
 struct TuneKey {
-    int storage, s2, walls, nz, rule;
+    int storage, s2, walls, nz, rule, collision;
     bool operator<(const TuneKey &o) const
     {
-        return std::make_tuple(storage, s2, walls, nz, rule) < std::make_tuple(o.storage, o.s2, o.walls, o.nz, o.rule);
+        return std::make_tuple(storage, s2, walls, nz, rule, collision) <
+               std::make_tuple(o.storage, o.s2, o.walls, o.nz, o.rule, o.collision);
     }
 };
 
@@ -534,7 +543,7 @@ int choose_tile(wdlb_lattice lat, double sigma, int32_t walls, const wdlb_option
 {
     if (!tiled_applies(lat, sigma, o)) return WDLB_TILE_8x8x8;
     if (o.tile >= 0) return o.tile;
-    const TuneKey key{o.storage, two_sigma(sigma), walls, lat.nz, o.shell_rule};
+    const TuneKey key{o.storage, two_sigma(sigma), walls, lat.nz, o.shell_rule, o.collision};
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) return it->second;
@@ -615,7 +624,7 @@ wdlb_status wdlb_create(wdlb_lattice lat, double sigma, int32_t walls, double ta
     build_ball(sigma, ctx->tab.ball);
     build_shell_rule(sigma, o.shell_rule, ctx->tab.shell, ctx->tab.wvec);
     ctx->tab.wshell = o.shell_rule == WDLB_SHELL_COMPACT ? 1.0 : ctx->tab.wvec[0];
-    ctx->L = &launchers_for(o.storage);
+    ctx->L = &launchers_for(o.storage, o.collision);
     set_params(ctx);
     ctx->kp.tile = choose_tile(lat, sigma, walls, o);
     ctx->kp.tiled = ctx->L->prepare(ctx->kp) ? 1 : 0;
@@ -1064,7 +1073,7 @@ wdlb_status wdlb_autotune(wdlb_lattice lat, double sigma, int32_t walls, const w
     double t[3];
     wdlb_status s = probe_tiles(lat, sigma, walls, o, &b, t);
     if (s != WDLB_OK) return s;
-    g_tune[TuneKey{o.storage, two_sigma(sigma), walls, lat.nz, o.shell_rule}] = b;
+    g_tune[TuneKey{o.storage, two_sigma(sigma), walls, lat.nz, o.shell_rule, o.collision}] = b;
     if (best) *best = b;
     if (ms)
         for (int v = 0; v < 3; v++) ms[v] = t[v];
@@ -1409,12 +1418,13 @@ wdlb_status wdlb_batch_create(const wdlb_options *opt, uint64_t pool_bytes, int3
         o = *opt;
     else
         wdlb_default_options(&o);
-    if (o.closure < 0 || o.closure > 2 || o.omega_mode < 0 || o.omega_mode > 1 || o.storage < 0 || o.storage > 2)
+    if (o.closure < 0 || o.closure > 2 || o.omega_mode < 0 || o.omega_mode > 1 || o.storage < 0 || o.storage > 2 ||
+        o.collision < 0 || o.collision > 1 || (o.collision == WDLB_COLLISION_DW && o.storage != WDLB_STORE_F32))
         return bfail(nullptr, WDLB_ERR_ARG, "invalid options");
     wdlb_batch *b = new (std::nothrow) wdlb_batch();
     if (!b) return bfail(nullptr, WDLB_ERR_OOM, "host allocation failed");
     b->opt = o;
-    b->L = &launchers_for(o.storage);
+    b->L = &launchers_for(o.storage, o.collision);
     b->slots.resize(max_pores);
     if (o.stream) {
         b->stream = static_cast<cudaStream_t>(o.stream);

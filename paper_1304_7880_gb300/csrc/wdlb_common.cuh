@@ -71,6 +71,11 @@ struct KParams {
     double h_off;            // half packing fraction of n_off: chi_of_n n_off / 2
     double ref_ng;           // n_ref g2(n_ref) (NBAR mode)
     double h_pred;           // kappa beta / 6: implicit factor of the field-velocity predictor per unit t
+    // g, omega and K/(2 c_s^4) (0 without fields) split into pairs of floats
+    // for the double-word collision (hi, lo)
+    float g_dw[3][2];
+    float omega_dw[2];
+    float ka_dw[2];
 };
 
 // Tiled ball sum: an 8 x 8 x 8 brick of nodes per block with a halo of

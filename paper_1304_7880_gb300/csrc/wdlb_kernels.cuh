@@ -33,6 +33,7 @@
 #pragma once
 
 #include "wdlb_common.cuh"
+#include "wdlb_dw.cuh"
 
 namespace wdlb {
 
@@ -125,9 +126,11 @@ __device__ __forceinline__ void moments_body(const KParams &p, const KBufs<S, ty
     const V4<T> old = b.nu[i];
     const T H = T(p.h_pred) * b.tprev[i];
     const T den = T(1) / (T(1) + H);
-    const T vx = ((jx + T(0.5) * (n * T(p.g[0]) + b.cprev[i])) * inv + H * old.y) * den;
-    const T vy = ((jy + T(0.5) * (n * T(p.g[1]) + b.cprev[p.Npad + i])) * inv + H * old.z) * den;
-    const T vz = ((jz + T(0.5) * (n * T(p.g[2]) + b.cprev[2 * p.Npad + i])) * inv + H * old.w) * den;
+    // every multiply-add written out, so each kernel that runs this body
+    // (the per-phase step and the persistent one) computes the same bits
+    const T vx = fma(H, old.y, fma(T(0.5), fma(n, T(p.g[0]), b.cprev[i]), jx) * inv) * den;
+    const T vy = fma(H, old.z, fma(T(0.5), fma(n, T(p.g[1]), b.cprev[p.Npad + i]), jy) * inv) * den;
+    const T vz = fma(H, old.w, fma(T(0.5), fma(n, T(p.g[2]), b.cprev[2 * p.Npad + i]), jz) * inv) * den;
     if (OUT) {
         if (out_n) out_n[i] = double(n);
         if (out_u) {
@@ -311,7 +314,7 @@ __device__ __forceinline__ void ball_brick_ct(const KParams &p, const V4<T> *nu,
 // - h_off; dh, dn: deviations of the two neighbours.  Besides Q+ and Q- it
 // returns Q+ - Q-, formed from the deviations so that it is accurate relative
 // to itself (it is what the mean-field sum accumulates):
-//   Q+ - Q- = G+ (dn+ - dn-) + (G+ - G-) n-,   G = 2 g2,
+//   Q+ - Q- = [(G+ + G-)(dn+ - dn-) + (G+ - G-)(n+ + n-)] / 2,   G = 2 g2,
 //   CS:  G+ - G- = (dh+ - dh-) [s+^2 + s-^2 + s+ s- (1 + s+ + s-)] / (s+^3 s-^3)
 //   PY:  G+ - G- = (dh+ - dh-) [3 (s+ + s-) - s+ s-] / (s+^2 s-^2)
 // (exact divided differences of the closures; s- - s+ = dh+ - dh-).
@@ -363,7 +366,12 @@ __device__ __forceinline__ void pair_weights(T s0, T noff, T dhp, T dnp, T dhm, 
     }
     qp = gp * np;
     qm = gm * nm;
-    qd = fma(gp, dnp - dnm, gd * nm);
+    // Q+ - Q- in the form that is odd under swapping the two ends bit for bit:
+    // (+e, -e) and its mirror image (-e, +e) swap the ends, so the mean-field sum
+    // cancels between mirror pairs exactly where the state is mirror-symmetric.
+    // (G+ (dn+ - dn-) + (G+ - G-) n- is the same number rounded differently at
+    // each end; in a driven slit that left a net x-force of 0.3 % of the drive.)
+    qd = T(0.5) * fma(add_rn(gp, gm), dnp - dnm, gd * add_rn(np, nm));
 }
 
 // Shell-sum accumulators (doubled weights Q = 2q, no quadrature weight w).
@@ -415,16 +423,18 @@ __device__ __forceinline__ void shell_forces(const KParams &p, const ShellAcc<T>
     const T wh = T(0.5) * T(p.wshell);
     const T mf = -T(CS2) * T(p.sig2) * wh * n;
     const T vi = T(p.beta) * wh * n;
-    Cx = mf * a.Vx + vi * a.Wx;
-    Cy = mf * a.Vy + vi * a.Wy;
-    Cz = mf * a.Vz + vi * a.Wz;
+    // multiply-adds written out (the same bits in every kernel); the product
+    // with the mean-field sum V, the larger term next to a wall, enters exactly
+    Cx = fma(mf, a.Vx, vi * a.Wx);
+    Cy = fma(mf, a.Vy, vi * a.Wy);
+    Cz = fma(mf, a.Vz, vi * a.Wz);
     const T pa = -(T(CS2) / T(5)) * T(p.sig2) * n * wh;
-    Axx = T(2) * pa * (a.Sxx - a.Vx * vx);
-    Ayy = T(2) * pa * (a.Syy - a.Vy * vy);
-    Azz = T(2) * pa * (a.Szz - a.Vz * vz);
-    Axy = pa * (a.Sxy - (a.Vy * vx + a.Vx * vy));
-    Axz = pa * (a.Sxz - (a.Vz * vx + a.Vx * vz));
-    Ayz = pa * (a.Syz - (a.Vz * vy + a.Vy * vz));
+    Axx = T(2) * pa * fma(-a.Vx, vx, a.Sxx);
+    Ayy = T(2) * pa * fma(-a.Vy, vy, a.Syy);
+    Azz = T(2) * pa * fma(-a.Vz, vz, a.Szz);
+    Axy = pa * (a.Sxy - fma(a.Vy, vx, a.Vx * vy));
+    Axz = pa * (a.Sxz - fma(a.Vz, vx, a.Vx * vz));
+    Ayz = pa * (a.Syz - fma(a.Vz, vy, a.Vy * vz));
     tsum = a.t * wh;
 }
 
@@ -540,6 +550,130 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
     b.tprev[i] = tsum;
 }
 
+// ---------------------------------------------------------------------------
+// Collision and push of node i as in collide_push, with the collision and the
+// re-encoding for the target in double-word arithmetic (FP32 storage): the
+// stored deviations, the fields and the results stay FP32.  In a driven slit
+// each step changes the momentum by a fraction ~ nu/H^2 of itself (2e-4 at
+// H = 159), so the ~6e-8 rounding of the FP32 collision is a few 1e-4 of the
+// per-step drive, and part of it acts as a steady spurious force; here the
+// collision's rounding sits ~2^-44 below its operands and the result is
+// rounded once, at the store.  Velocity components that are zero for a
+// lattice direction are skipped at compile time.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dwf dw_signed(int c, dwf a) { return c > 0 ? a : -a; }
+
+// c . (a, b, c3) for a lattice direction with components in {-1, 0, 1}
+__device__ __forceinline__ dwf dw_cdot(int cx, int cy, int cz, dwf a, dwf b, dwf c)
+{
+    if (cx) {
+        dwf r = dw_signed(cx, a);
+        if (cy) r = r + dw_signed(cy, b);
+        if (cz) r = r + dw_signed(cz, c);
+        return r;
+    }
+    if (cy) {
+        dwf r = dw_signed(cy, b);
+        if (cz) r = r + dw_signed(cz, c);
+        return r;
+    }
+    return cz ? dw_signed(cz, c) : dw_from(0.f);
+}
+
+template <class S, int CL, bool WALLS, class TargetDn>
+__device__ __forceinline__ void collide_push_dw(const KParams &p, const KBufs<S, float> &b, int i, int x, int y,
+                                                int z, float hr, float Cx, float Cy, float Cz, float Axx, float Ayy,
+                                                float Azz, float Axy, float Axz, float Ayz, float tsum, float dn_self,
+                                                TargetDn target_dn)
+{
+    static_assert(sizeof(S) == sizeof(float), "double-word collision: FP32 storage");
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const float noff = float(p.n_off);
+    const float dsc = b.nscale[i];
+    float d[NQ];
+    dwf dn = dw_from(0.f), jx = dw_from(0.f), jy = dw_from(0.f), jz = dw_from(0.f);
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        d[q] = Store<S>::load(b.f_in + (size_t)q * p.Npad + i, 0.f);
+        dn += d[q];
+        if (cx_of(q)) jx += cx_of(q) > 0 ? d[q] : -d[q];
+        if (cy_of(q)) jy += cy_of(q) > 0 ? d[q] : -d[q];
+        if (cz_of(q)) jz += cz_of(q) > 0 ? d[q] : -d[q];
+    }
+    const dwf n = two_sum(noff, dsc) + dn;
+    const dwf inv_n = dw_from(1.f) / n;
+
+    // collision velocity u = (j + F/2)/n with F = n g + C
+    const dwf Fx = n * dw_load(p.g_dw[0]) + Cx, Fy = n * dw_load(p.g_dw[1]) + Cy, Fz = n * dw_load(p.g_dw[2]) + Cz;
+    const dwf ux = (jx + Fx * 0.5f) * inv_n;
+    const dwf uy = (jy + Fy * 0.5f) * inv_n;
+    const dwf uz = (jz + Fz * 0.5f) * inv_n;
+
+    dwf omega = dw_load(p.omega_dw);
+    if (p.omega_mode == 1) {
+        const float chib = 2.f * hr;
+        const float loc = chib / float(p.chi_of_n) * contact_g<CL, float>(chib);
+        float tau = loc > 0.f ? 0.5f + (float(p.tau) - 0.5f) * float(p.ref_ng) / loc : 1e30f;
+        tau = tau < 0.501f ? 0.501f : tau;
+        omega = dw_from(1.f) / dw_from(tau);
+    }
+
+    const dwf tr3 = (two_sum(Axx, Ayy) + Azz) * dw_const(1.0 / 3.0);
+    const dwf Bxx = Axx - tr3, Byy = Ayy - tr3, Bzz = Azz - tr3;   // traceless A
+    const dwf kA = dw_load(p.ka_dw);                               // K / (2 c_s^4), 0 without fields
+    const dwf uu15 = (ux * ux + uy * uy + uz * uz) * 1.5f;
+    const dwf uF = ux * Fx + uy * Fy + uz * Fz;
+    const dwf src_pref = dw_from(1.f) - omega * 0.5f;
+    const int nxy = nx * ny;
+    const bool inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && (WALLS || (z > 0 && z < nz - 1));
+
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        const int cxq = cx_of(q), cyq = cy_of(q), czq = cz_of(q);
+        const dwf wq = dw_const(w_of(q));
+        const dwf cu = dw_cdot(cxq, cyq, czq, ux, uy, uz);
+        const dwf cF = dw_cdot(cxq, cyq, czq, Fx, Fy, Fz);
+        const dwf feq_dev = wq * (dn + n * (cu * 3.f + (cu * cu) * 4.5f - uu15));
+        const dwf phi = wq * ((cF - uF) * 3.f + (cu * cF) * 9.f);
+        dwf cAc = dw_from(0.f);
+        if (cxq) cAc = cAc + Bxx;
+        if (cyq) cAc = cAc + Byy;
+        if (czq) cAc = cAc + Bzz;
+        if (cxq && cyq) cAc = cAc + float(2 * cxq * cyq) * Axy;
+        if (cxq && czq) cAc = cAc + float(2 * cxq * czq) * Axz;
+        if (cyq && czq) cAc = cAc + float(2 * cyq * czq) * Ayz;
+        const dwf sa = kA * wq * cAc;
+        const dwf post = d[q] - omega * (d[q] - feq_dev) + src_pref * (phi + sa);
+        int zt = z + czq;
+        int dst;
+        int qq = q;
+        float dn_t;
+        if (WALLS && (zt == 0 || zt == nz - 1)) {
+            dst = i;
+            qq = opp_of(q);
+            dn_t = dn_self;
+        } else {
+            if (inner) {
+                dst = i + cxq + cyq * nx + czq * nxy;
+            } else {
+                if (!WALLS) zt = wrap_coord(zt, nz);
+                const int xt = wrap_coord(x + cxq, nx);
+                const int yt = wrap_coord(y + cyq, ny);
+                dst = xt + nx * (yt + ny * zt);
+            }
+            dn_t = q == 0 ? dn_self : target_dn(q, dst);
+        }
+        if (!in_bounds(dst, p.N, b.status)) continue;
+        const float stored = dw_round(post + wq * two_sum(dsc, -dn_t));
+        Store<S>::put(b.f_out + (size_t)qq * p.Npad + dst, stored, 0.f);
+    }
+    b.nscale[i] = dn_self;
+    b.cprev[i] = Cx;
+    b.cprev[p.Npad + i] = Cy;
+    b.cprev[2 * p.Npad + i] = Cz;
+    b.tprev[i] = tsum;
+}
+
 // Shell sums of node (x, y, z) with the table in global memory (any sigma,
 // any lattice shape): the (+e, -e) pairs of the library's table, neighbours
 // wrapped periodically in x, y (and z without walls), n = 0 on and beyond the
@@ -593,7 +727,7 @@ __device__ __forceinline__ void shell_sums_generic(const KParams &p, const V4<T>
 // Fields + collision + streaming, one node per thread, shell table from
 // global memory (any sigma and lattice shape).
 // ---------------------------------------------------------------------------
-template <class S, int CL, bool WALLS, bool FIELDS, bool WT = false>
+template <class S, int CL, bool WALLS, bool FIELDS, bool WT = false, class A = typename Store<S>::T>
 __device__ __forceinline__ void shell_body(const KParams &p, const KBufs<S, typename Store<S>::T> &b, int blk)
 {
     typedef typename Store<S>::T T;
@@ -621,10 +755,13 @@ __device__ __forceinline__ void shell_body(const KParams &p, const KBufs<S, type
                                              b.status);
         shell_forces<T>(p, a, n, vx, vy, vz, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum);
     }
-    collide_push<S, CL, WALLS, FIELDS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
-                                       [&](int, int dst) {
-                                           return in_bounds(dst, p.N, b.status) ? b.nu[dst].x : T(0);
-                                       });
+    const auto target_dn = [&](int, int dst) { return in_bounds(dst, p.N, b.status) ? b.nu[dst].x : T(0); };
+    if constexpr (is_dw<A>::value && !FIELDS)
+        collide_push_dw<S, CL, WALLS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
+                                      target_dn);
+    else
+        collide_push<S, CL, WALLS, FIELDS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum,
+                                           me.x, target_dn);
 }
 
 template <class S, int CL, bool WALLS, bool FIELDS, bool WT>

@@ -24,6 +24,17 @@ typedef float S;
 typedef __half S;
 #endif
 typedef Store<S>::T T;
+// arithmetic of the collision: the storage's compute type, or (built with
+// WDLB_DW_COLLISION, FP32 storage only) double-word pairs of floats
+#if WDLB_DW_COLLISION
+static_assert(WDLB_STORAGE == 1, "the double-word collision is built for FP32 storage");
+typedef dwf A;
+#else
+typedef T A;
+#endif
+// the double-word collision is compiled for lattices with walls only (the
+// library refuses it for periodic boxes, which FP32 already serves at 1e-5)
+constexpr bool kPeriodic = !is_dw<A>::value;
 
 constexpr int kThreads = 256;
 
@@ -63,14 +74,17 @@ void launch_fields_shell(const KParams &p, const KBufs<S, T> &b, cudaStream_t st
 template <int S2, int V, bool WALLS, bool WT>
 cudaError_t tiled_attr()
 {
-    return cudaFuncSetAttribute(k_step_shell_tiled<S, S2, V, WALLS, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_step_shell_tiled<S, S2, V, WALLS, WT, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)tiled::smem_bytes<S2, V, WT>());
 }
 
 template <int S2, int V, bool WT>
 cudaError_t tiled_attr_w(bool walls)
 {
-    return walls ? tiled_attr<S2, V, true, WT>() : tiled_attr<S2, V, false, WT>();
+    if constexpr (kPeriodic)
+        return walls ? tiled_attr<S2, V, true, WT>() : tiled_attr<S2, V, false, WT>();
+    else
+        return walls ? tiled_attr<S2, V, true, WT>() : cudaErrorNotSupported;
 }
 
 template <int S2, bool WT>
@@ -89,7 +103,7 @@ cudaError_t tiled_attr_r(int v, bool walls, bool wt)
 template <int S2, int V, bool WALLS, bool WT>
 void launch_tiled_group(const BatchLaunch &L, const KBufs<S, float> *B, const BatchGroup &G, cudaStream_t st)
 {
-    k_step_shell_tiled<S, S2, V, WALLS, WT>
+    k_step_shell_tiled<S, S2, V, WALLS, WT, A>
         <<<G.nitems, tiled::threads_of(V), tiled::smem_bytes<S2, V, WT>(), st>>>(L.params, B, G.items);
 }
 
@@ -98,7 +112,7 @@ void launch_tiled_r(const BatchLaunch &L, const KBufs<S, float> *B, const BatchG
 {
     if (G.walls)
         launch_tiled_group<S2, V, true, WT>(L, B, G, st);
-    else
+    else if constexpr (kPeriodic)
         launch_tiled_group<S2, V, false, WT>(L, B, G, st);
 }
 
@@ -286,13 +300,19 @@ cudaError_t do_batch_step(const BatchLaunch &L, int parity, int part, int group,
 #define WDLB_SB(CLV, WV)                                                                         \
     do {                                                                                         \
         if (G.rule)                                                                              \
-            k_step_shell<S, CLV, WV, true><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items);  \
+            k_step_shell<S, CLV, WV, true, A><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items);  \
         else                                                                                     \
-            k_step_shell<S, CLV, WV, false><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items); \
+            k_step_shell<S, CLV, WV, false, A><<<G.nitems, kThreads, 0, st>>>(L.params, B, G.items); \
     } while (0)
-        if (G.closure == 0) { if (G.walls) WDLB_SB(0, true); else WDLB_SB(0, false); }
-        else if (G.closure == 1) { if (G.walls) WDLB_SB(1, true); else WDLB_SB(1, false); }
-        else { if (G.walls) WDLB_SB(2, true); else WDLB_SB(2, false); }
+        if (G.walls) {
+            if (G.closure == 0) WDLB_SB(0, true);
+            else if (G.closure == 1) WDLB_SB(1, true);
+            else WDLB_SB(2, true);
+        } else if constexpr (kPeriodic) {
+            if (G.closure == 0) WDLB_SB(0, false);
+            else if (G.closure == 1) WDLB_SB(1, false);
+            else WDLB_SB(2, false);
+        }
 #undef WDLB_SB
         *launches += 1;
     }
@@ -315,7 +335,7 @@ bool do_flow_ok(const BatchLaunch &L)
 template <bool WALLS, bool WT>
 cudaError_t launch_flow(const BatchLaunch &L, const FlowLaunch &F, cudaStream_t st)
 {
-    auto kern = k_step_flow<S, 8, 2, WALLS, WT>;
+    auto kern = k_step_flow<S, 8, 2, WALLS, WT, A>;
     const size_t smem = flow_smem_bytes<8, 2, WT>();
     static int grid = 0;   // one per template instance: resident blocks on the whole GPU
     if (grid == 0) {
@@ -353,8 +373,11 @@ cudaError_t do_flow_step(const BatchLaunch &L, const FlowLaunch &F, cudaStream_t
 #if WDLB_STORAGE != 0
     if (!do_flow_ok(L)) return cudaErrorInvalidValue;
     const BatchGroup &G = L.groups[0];
-    cudaError_t e = G.walls ? (G.rule ? launch_flow<true, true>(L, F, st) : launch_flow<true, false>(L, F, st))
-                            : (G.rule ? launch_flow<false, true>(L, F, st) : launch_flow<false, false>(L, F, st));
+    cudaError_t e = cudaErrorNotSupported;
+    if (G.walls)
+        e = G.rule ? launch_flow<true, true>(L, F, st) : launch_flow<true, false>(L, F, st);
+    else if constexpr (kPeriodic)
+        e = G.rule ? launch_flow<false, true>(L, F, st) : launch_flow<false, false>(L, F, st);
     *launches += 1;
     return e;
 #else
@@ -383,6 +406,8 @@ cudaError_t launch_sum_density(const KParams &p, const double *d_n, double *part
     *launches += 2;
     return cudaGetLastError();
 }
+#elif WDLB_STORAGE == 1 && WDLB_DW_COLLISION
+const Launchers &launchers_f32dw() { return kL; }
 #elif WDLB_STORAGE == 1
 const Launchers &launchers_f32() { return kL; }
 #else

@@ -115,6 +115,8 @@ struct Launchers {
 
 const Launchers &launchers_f64();
 const Launchers &launchers_f32();
+// FP32 storage with the collision in double-word arithmetic (WDLB_COLLISION_DW)
+const Launchers &launchers_f32dw();
 const Launchers &launchers_f16();
 
 // FP64 sum of d_n over fluid nodes into *result (device), one launch pair.

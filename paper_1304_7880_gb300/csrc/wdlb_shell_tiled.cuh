@@ -237,17 +237,18 @@ constexpr bool tma_staging()
 // blocks' shared memory fits (227 KB per SM; the compiler then keeps to 85
 // registers per thread), else two where two fit, else one; one for 512
 // threads.  Three blocks measured 7-12 % faster than two for sigma 3 (8^3
-// bricks) and sigma 4 (8 x 8 x 4 bricks).
-template <int S2, int V, bool WT = false>
+// bricks) and sigma 4 (8 x 8 x 4 bricks).  The double-word collision (DW)
+// needs more than 85 registers: at most two blocks.
+template <int S2, int V, bool WT = false, bool DW = false>
 constexpr int blocks_per_sm()
 {
     return threads_of(V) != 256                                ? 1
-           : 3 * smem_bytes<S2, V, WT>() <= size_t(227) * 1024 ? 3
+           : !DW && 3 * smem_bytes<S2, V, WT>() <= size_t(227) * 1024 ? 3
            : 2 * smem_bytes<S2, V, WT>() <= size_t(227) * 1024 ? 2
                                                                 : 1;
 }
 
-template <class S, int S2, int V, int CL, bool WALLS, bool FIELDS, bool WT = false>
+template <class S, int S2, int V, int CL, bool WALLS, bool FIELDS, bool WT = false, class A = float>
 __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, float> &b, int bx, int by, int bz)
 {
     constexpr int R = shell_radius(S2);
@@ -426,12 +427,16 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
             shell_forces<float>(p, a, noff + me.x, me.y, me.z, me.w, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz,
                                 tsum);
         }
-        collide_push<S, CL, WALLS, FIELDS>(
-            p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum, me.x,
-            [&](int q, int) {
-                const int k = base + cx_of(q) + SX * (cy_of(q) + SY * cz_of(q));
-                return in_bounds(k, NS, b.status) ? sm4[k].x : 0.f;
-            });
+        const auto target_dn = [&](int q, int) {
+            const int k = base + cx_of(q) + SX * (cy_of(q) + SY * cz_of(q));
+            return in_bounds(k, NS, b.status) ? sm4[k].x : 0.f;
+        };
+        if constexpr (is_dw<A>::value && !FIELDS)
+            collide_push_dw<S, CL, WALLS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz, tsum,
+                                          me.x, target_dn);
+        else
+            collide_push<S, CL, WALLS, FIELDS>(p, b, i, x, y, z, hr, Cx, Cy, Cz, Axx, Ayy, Azz, Axy, Axz, Ayz,
+                                               tsum, me.x, target_dn);
     }
 }
 

@@ -49,24 +49,24 @@ __global__ void __launch_bounds__(256) k_step_ball_tiled(const KParams *P, const
     }
 }
 
-template <class S, int CL, bool WALLS, bool WT>
+template <class S, int CL, bool WALLS, bool WT, class A = typename Store<S>::T>
 __global__ void __launch_bounds__(256) k_step_shell(const KParams *P, const KBufs<S, typename Store<S>::T> *B,
                                                     const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
     const KParams p = P[w.slot];
     const KBufs<S, typename Store<S>::T> b = B[w.slot];
-    shell_body<S, CL, WALLS, false, WT>(p, b, w.bx);
+    shell_body<S, CL, WALLS, false, WT, A>(p, b, w.bx);
 }
 
-template <class S, int S2, int V, bool WALLS, bool WT>
-__global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2, V, WT>()))
+template <class S, int S2, int V, bool WALLS, bool WT, class A = float>
+__global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2, V, WT, is_dw<A>::value>()))
     k_step_shell_tiled(const KParams *P, const KBufs<S, float> *B, const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
     const KParams p = P[w.slot];
     const KBufs<S, float> b = B[w.slot];
-    tiled::tiled_body<S, S2, V, 0, WALLS, false, WT>(p, b, w.bx, w.by, w.bz);
+    tiled::tiled_body<S, S2, V, 0, WALLS, false, WT, A>(p, b, w.bx, w.by, w.bz);
 }
 
 }  // namespace wdlb
@@ -120,8 +120,8 @@ __device__ __forceinline__ int ld_acquire_gpu(const int *p)
     return v;
 }
 
-template <class S, int S2, int V, bool WALLS, bool WT>
-__global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2, V, WT>()))
+template <class S, int S2, int V, bool WALLS, bool WT, class A = float>
+__global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2, V, WT, is_dw<A>::value>()))
     k_step_flow(FlowArgs a)
 {
     typedef typename Store<S>::T T;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2
         else if (phase == 1)
             ball_brick_ct<T, S2>(p, b.nu, b.hb, b.status, w.bx, w.by, w.bz);
         else
-            tiled::tiled_body<S, S2, V, 0, WALLS, false, WT>(p, b, w.bx, w.by, w.bz);
+            tiled::tiled_body<S, S2, V, 0, WALLS, false, WT, A>(p, b, w.bx, w.by, w.bz);
         __syncthreads();       // every thread's writes of this item are done
         if (threadIdx.x == 0) {
             __threadfence();   // release them before counting the item as done

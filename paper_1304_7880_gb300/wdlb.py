@@ -46,10 +46,13 @@ class wdlb_options(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("tile", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("shell_rule", ctypes.c_int32), ("staging", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
-                ("persistent", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("collision", ctypes.c_int32)]
 
 
 STAGINGS = {"auto": 0, "cp_async": 1}
+# arithmetic of the collision with FP32 storage: "fp32", or "dw" (double-word
+# pairs of floats; lattices with walls)
+COLLISIONS = {"fp32": 0, "dw": 1}
 
 
 class wdlb_pore_desc(ctypes.Structure):
@@ -175,12 +178,13 @@ class Context:
 
 def wdlb_create(lattice, sigma, walls, tau, g=(0.0, 0.0, 0.0), closure="CS", omega_mode="const",
                 storage="f32", interactions=True, k_cross=2.0, n_ref=0.0, device=None, tile=-1, autotune=True,
-                shell_rule="full", staging="auto", wait_limit=0):
+                shell_rule="full", staging="auto", wait_limit=0, collision="fp32"):
     """Create a context; device memory and stream come from PyTorch.  tile: -1
     (autotuner) or a forced tile shape 0, 1, 2 of the tiled shell kernel;
     shell_rule: "full" or "compact" contact-shell quadrature; staging: "auto"
     (TMA tiles where possible) or "cp_async"; wait_limit: polls of the TMA
-    tile's wait (0: the library's default)."""
+    tile's wait (0: the library's default); collision: "fp32" or "dw"
+    (double-word collision, FP32 storage with walls)."""
     import torch
 
     lib = load_library()
@@ -199,6 +203,7 @@ def wdlb_create(lattice, sigma, walls, tau, g=(0.0, 0.0, 0.0), closure="CS", ome
     opt.shell_rule = SHELL_RULES[shell_rule]
     opt.staging = STAGINGS[staging]
     opt.wait_limit = int(wait_limit)
+    opt.collision = COLLISIONS[collision]
     walls_i = 1 if walls else 0
     nbytes = ctypes.c_uint64()
     _check(lib.wdlb_workspace_size(lat, float(sigma), walls_i, ctypes.byref(opt), ctypes.byref(nbytes)))
@@ -291,10 +296,10 @@ def wdlb_load_state(ctx: Context, buf: np.ndarray):
     _check(load_library().wdlb_load_state(ctx.handle, _ptr(buf), ctypes.c_uint64(buf.nbytes)), ctx)
 
 
-def wdlb_autotune(lattice, sigma, walls, storage="f32", device=None, shell_rule="full"):
+def wdlb_autotune(lattice, sigma, walls, storage="f32", device=None, shell_rule="full", collision="fp32"):
     """Time the tiled shell kernel's shapes for this (storage, sigma, walls, nz,
-    shell rule) now and record the fastest; returns (best, [ms per step of
-    shapes 0, 1, 2])."""
+    shell rule, collision) now and record the fastest; returns (best, [ms per
+    step of shapes 0, 1, 2])."""
     import torch
 
     lib = load_library()
@@ -302,6 +307,7 @@ def wdlb_autotune(lattice, sigma, walls, storage="f32", device=None, shell_rule=
     lib.wdlb_default_options(ctypes.byref(opt))
     opt.storage = STORAGES[storage]
     opt.shell_rule = SHELL_RULES[shell_rule]
+    opt.collision = COLLISIONS[collision]
     nx, ny, nz = (int(v) for v in lattice)
     best = ctypes.c_int32()
     ms = (ctypes.c_double * 3)()
@@ -468,12 +474,13 @@ def _bcheck(status, batch=None):
 
 def wdlb_batch_create(max_pores, pool_bytes, closure="CS", omega_mode="const", storage="f32", interactions=True,
                       k_cross=2.0, device=None, shell_rule="full", autotune=True, staging="auto",
-                      persistent=False, wait_limit=0):
+                      persistent=False, wait_limit=0, collision="fp32"):
     import torch
 
     lib = load_library()
     opt = wdlb_options()
     lib.wdlb_default_options(ctypes.byref(opt))
+    opt.collision = COLLISIONS[collision]
     opt.closure = CLOSURES[closure]
     opt.omega_mode = OMEGA_MODES[omega_mode]
     opt.storage = STORAGES[storage]
@@ -593,13 +600,14 @@ class Server:
 
 
 def wdlb_server_create(hbm_budget, max_active=256, check_every=100, closure="CS", storage="f32", device=None,
-                       shell_rule="full"):
+                       shell_rule="full", collision="fp32"):
     """Serving loop (native worker thread) over a batch whose pool is a torch tensor."""
     import torch
 
     lib = load_library()
     opt = wdlb_options()
     lib.wdlb_default_options(ctypes.byref(opt))
+    opt.collision = COLLISIONS[collision]
     opt.closure = CLOSURES[closure]
     opt.storage = STORAGES[storage]
     opt.shell_rule = SHELL_RULES[shell_rule]

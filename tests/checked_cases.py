@@ -30,6 +30,16 @@ SINGLE = {
     "s8_bulk_compact": ((16, 16, 20), 8.0, False, "f32", "compact"),
     "narrow_pore_s4": ((6, 5, 21), 4.0, True, "f32", "full"),
 }
+# the double-word collision (slits only): tiled kernels on every tile shape and
+# the generic kernel (sigma 3.5, and a pore too narrow for the tiled kernel)
+DW_CASES = {
+    "s4_slit_dw_t%d": ((10, 8, 27), 4.0, True, "f32", "full"),
+    "s6_slit_compact_dw_t%d": ((12, 9, 35), 6.0, True, "f32", "compact"),
+}
+DW_SINGLE = {
+    "s3.5_slit_dw": ((11, 9, 15), 3.5, True, "f32", "full"),
+    "narrow_pore_s4_dw": ((6, 5, 21), 4.0, True, "f32", "full"),
+}
 
 
 def state(lat, sigma, walls, seed):
@@ -37,10 +47,10 @@ def state(lat, sigma, walls, seed):
     return synth.uniform_with_noise(nx, ny, nz, 0.4 / sigma ** 3, 2e-2, seed, walls)
 
 
-def run_case(lat, sigma, walls, storage, rule, tile):
+def run_case(lat, sigma, walls, storage, rule, tile, collision="fp32"):
     n, u = state(lat, sigma, walls, 7)
     ctx = w.wdlb_create(lat, sigma, walls, 1.0, (1e-5, 0.0, 0.0), storage=storage, shell_rule=rule, tile=tile,
-                        autotune=False)
+                        autotune=False, collision=collision)
     w.wdlb_init_fields(ctx, n, u)
     w.wdlb_step(ctx, 5)
     w.wdlb_moments(ctx)          # raises on the checked build's bounds flag
@@ -56,6 +66,11 @@ def main(out):
             res[name % tile] = run_case(lat, sigma, walls, storage, rule, tile)
     for name, (lat, sigma, walls, storage, rule) in SINGLE.items():
         res[name] = run_case(lat, sigma, walls, storage, rule, -1)
+    for name, (lat, sigma, walls, storage, rule) in DW_CASES.items():
+        for tile in (0, 1, 2):
+            res[name % tile] = run_case(lat, sigma, walls, storage, rule, tile, "dw")
+    for name, (lat, sigma, walls, storage, rule) in DW_SINGLE.items():
+        res[name] = run_case(lat, sigma, walls, storage, rule, -1, "dw")
     # a batch of pores with different kernels (tiled sigma 3 and 4, generic narrow pore)
     b = w.wdlb_batch_create(4, 64 << 20, storage="f32")
     slots = []

@@ -19,11 +19,16 @@
  *   df  pair weights, accumulators and forces in double, collision in float;
  *   dd  all of it in double.
  * Nodes within `band` layers of a wall take the variant `band_mode`, the rest
- * `inner_mode`.
+ * `inner_mode`.  `qd` picks the form of Q+ - Q- in the mean-field sum: sym (the
+ * kernel's, odd under swapping the pair's ends bit for bit) or asym (the
+ * earlier form, which rounds differently at the two ends).
  *
- *   column <nz> <n*> <sigma> <tau> <g_x> <steps> <band> <band_mode> <inner_mode>
+ *   column <nz> <n*> <sigma> <tau> <g_x> <steps> <band> <band_mode> <inner_mode> <qd>
  *
- * prints, per node z: n, v_x, v_z (the field velocity) after the steps.
+ * prints, per node z: n, v_x, v_z (the field velocity) after the steps, and on
+ * stderr the x-momentum balance of the last step's fields: "xforce S D" with S
+ * the column's sum of C_x (zero in exact arithmetic: the pair forces conserve
+ * momentum) and D the sum of the driving force n g_x.
  */
 #include <math.h>
 #include <stdio.h>
@@ -43,6 +48,8 @@ static double SIG, TAU, GX, PK[128][3], WSH, NOFF, HOFF, CHIN, CHALF, BETA, HPRE
 static STORE *f[2][Q], *nudn, *nuv[3], *hb, *cprev[3], *tprev;
 static double *nscale;
 static int cur = 0;
+static int QD_ASYM = 0;
+static double XF_INNER, XF_DRIVE;
 
 /* D3Q19 in the library's order: rest, faces, edges (Sec. 5). */
 static void d3q19(void)
@@ -181,10 +188,11 @@ static node_fn variant(const char *s)
 
 int main(int argc, char **argv)
 {
-    if (argc != 10) {
-        fprintf(stderr, "column <nz> <n*> <sigma> <tau> <g_x> <steps> <band> <band_mode> <inner_mode>\n");
+    if (argc != 11 || (strcmp(argv[10], "sym") && strcmp(argv[10], "asym"))) {
+        fprintf(stderr, "column <nz> <n*> <sigma> <tau> <g_x> <steps> <band> <band_mode> <inner_mode> <sym|asym>\n");
         return 2;
     }
+    QD_ASYM = !strcmp(argv[10], "asym");
     NZ = atoi(argv[1]);
     double nstar = atof(argv[2]);
     SIG = atof(argv[3]);
@@ -220,11 +228,13 @@ int main(int argc, char **argv)
         ball();
         int nxt = cur ^ 1;
         for (int q = 0; q < Q; q++) memset(f[nxt][q], 0, NZ * sizeof(STORE));
+        XF_INNER = XF_DRIVE = 0;
         for (int z = 1; z < NZ - 1; z++) (z <= band || z >= NZ - 1 - band ? in_band : inner)(z, nxt, new_nscale);
         for (int z = 1; z < NZ - 1; z++) nscale[z] = new_nscale[z];
         cur = nxt;
     }
     moments();
+    fprintf(stderr, "xforce %.9g %.9g\n", XF_INNER, XF_DRIVE);
     for (int z = 0; z < NZ; z++) printf("%.17g %.17g %.17g\n", NOFF + (double)nudn[z], (double)nuv[0][z], (double)nuv[2][z]);
     return 0;
 }

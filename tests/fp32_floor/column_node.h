@@ -3,7 +3,9 @@
  * with the exact divided difference of the closure, accumulators in table
  * order, second-order forcing with the A-term.  Included by column.c once per
  * precision variant: TW is the type of the pair weights, accumulators and
- * forces, TC the type of the collision, FETCH the neighbour loader of type TW. */
+ * forces, TC the type of the collision, FETCH the neighbour loader of type TW.
+ * Q+ - Q- takes the kernel's form, odd under swapping the pair's ends bit for
+ * bit, or (QD_ASYM) the earlier G+ (dn+ - dn-) + (G+ - G-) n-. */
         TW noff=(TW)NOFF, hoff=(TW)HOFF, hr = hoff + (TW)hb[z], s0 = (TW)1 - hr - hoff;
         TW me_dn=(TW)nudn[z], vx=(TW)nuv[0][z], vy=(TW)nuv[1][z], vz=(TW)nuv[2][z];
         TW Vx=0,Vy=0,Vz=0,Wx=0,Wy=0,Wz=0,Sxx=0,Syy=0,Szz=0,Sxy=0,Sxz=0,Syz=0,t=0;
@@ -14,7 +16,7 @@
             TW rp=(TW)1/(sp2*sp), rm=(TW)1/(sm2*sm);
             TW gp=fma(sp,rp,rp), gm=fma(sm,rm,rm);
             TW gd=(ghp-ghm)*((sp2+sm2)+fma(spm,sp+sm,spm))*(rp*rm);
-            TW qp=gp*np, qm=gm*nm, qd=fma(gp,gdnp-gdnm,gd*nm);
+            TW qp=gp*np, qm=gm*nm, qd=QD_ASYM ? fma(gp,gdnp-gdnm,gd*nm) : (TW)0.5*fma(gp+gm,gdnp-gdnm,gd*(np+nm));
             TW kx=(TW)PK[m][0], ky=(TW)PK[m][1], kz=(TW)PK[m][2];
             TW px=qp*(TW)vp[0],py=qp*(TW)vp[1],pz=qp*(TW)vp[2];
             TW dx=fma(-qm,(TW)vm[0],px),dy=fma(-qm,(TW)vm[1],py),dz=fma(-qm,(TW)vm[2],pz);
@@ -38,6 +40,7 @@
         for(int q=0;q<Q;q++){d[q]=(TC)f[cur][q][z];dn+=d[q];for(int a=0;a<3;a++)if(C[q][a])j[a]+=(TC)C[q][a]*d[q];}
         TC nn=sc+dn, inv=(TC)1/nn;
         TC F[3]={nn*(TC)GX+(TC)Cx, (TC)Cy, (TC)Cz};
+        XF_INNER += (double)Cx; XF_DRIVE += (double)(nn*(TC)GX);
         TC u[3]; for(int a=0;a<3;a++) u[a]=(j[a]+(TC)0.5*F[a])*inv;
         TC om=(TC)(1.0/TAU), tr3=((TC)Axx+(TC)Ayy+(TC)Azz)*(TC)(1.0/3);
         TC Bxx=(TC)Axx-tr3,Byy=(TC)Ayy-tr3,Bzz=(TC)Azz-tr3, kA=(TC)2*(TC)4.5;

@@ -4,12 +4,12 @@ the same seeded inputs.
 Tolerances (stated per storage and workload):
   FP64 storage and arithmetic: 1e-10 relative (summation order only).
   FP32: max relative error 1e-5 on n; on u, 1e-5 of max|u|, for bulk boxes.
-  FP32 in the driven slit (g_x = 1e-6, walls): n 1e-6, pore flux and u 5e-4
-  of max|u_x|.  Next to the walls the populations and the collision carry
-  force-driven parts of O(0.1) w n (the wall force per particle is ~0.14 in
-  lattice units while the driven flow is ~1e-4), which FP32 resolves to
-  ~eps * 0.1 w n per step; the measured floor is 2.4e-4 of max|u_x| after
-  1000 steps (n 1.5e-7, mean density 6e-8).
+  FP32 in the driven slit (g_x = 1e-6, walls): n 1e-6, pore flux 1e-5, u_x
+  1e-4 and every component of u 5e-4 of max|u_x|.  The largest pointwise
+  error is in u_z, which is zero at steady state: next to a wall the stored
+  populations carry a momentum j_z = -F_z/2 of ~1e-3 that u_z = (j_z + F_z/2)/n
+  cancels, so FP32 storage leaves u_z a noise of ~1e-4 of max|u_x| even with
+  exact arithmetic (the column emulator of tests/fp32_floor pins this).
   FP16 relative-deviation storage (10-bit mantissa): bulk n 1e-6, u 5e-3 of
   max|u|; refused in slits (steady-state u_x errors of 2 to 15 %).
 """
@@ -23,7 +23,7 @@ from paper_1304_7880_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": (1e-10, 1e-10), "f32": (1e-5, 1e-5), "f16": (1e-6, 5e-3)}
-TOL_SLIT = {"f32": (1e-6, 5e-4, 5e-4)}
+TOL_SLIT = {"f32": (1e-6, 5e-4, 1e-5, 1e-4)}   # n, any u, flux, u_x
 
 
 @pytest.fixture(scope="module")
@@ -129,15 +129,20 @@ def test_slit_8x8x41_reduced_precision(w, oracle_mod, storage):
     for _ in range(10):
         w.wdlb_step(ctx, 100)
         o.step(100)
-    tn, tu, tf = TOL_SLIT[storage]
+    tn, tu, tf, tux = TOL_SLIT[storage]
     en, eu = compare(ctx, o, True, storage, w, tol=(tn, tu))
     st = w.wdlb_pore_average(ctx)
+    n_g, u_g = w.wdlb_moments(ctx)
     n_o, u_o = o.moments()
+    m = fluid_mask(n_o.shape, True)
+    umax = np.abs(u_o[0, m]).max()
+    ec = [np.abs(u_g[a, m] - u_o[a, m]).max() / umax for a in range(3)]
     ref = oracle_mod.pore_average(n_o, u_o, True, p["g"][0])
     ef = abs(st["flux_x"] - ref["flux_x"]) / abs(ref["flux_x"])
     em = abs(st["mean_n"] - ref["mean_n"]) / ref["mean_n"]
-    print("%s 8x8x41 1000 steps: n err %.2e, u err %.2e, flux err %.2e, mean n err %.2e" % (storage, en, eu, ef, em))
-    assert ef <= tf and em <= tn
+    print("%s 8x8x41 1000 steps: n err %.2e, u err %.2e (u_x %.2e, u_y %.2e, u_z %.2e), flux err %.2e, "
+          "mean n err %.2e" % (storage, en, eu, ec[0], ec[1], ec[2], ef, em))
+    assert ef <= tf and em <= tn and ec[0] <= tux
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
