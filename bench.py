@@ -142,7 +142,7 @@ def kernel_source_hash():
     build flags (host-side launch code does not change a kernel's traffic)."""
     h = hashlib.sha256()
     pkg = os.path.join(ROOT, "paper_1304_7880_gb300")
-    for f in ("csrc/wdlb_common.cuh", "csrc/wdlb_kernels.cuh", "csrc/wdlb_shell_tiled.cuh",
+    for f in ("csrc/wdlb_common.cuh", "csrc/wdlb_dw.cuh", "csrc/wdlb_kernels.cuh", "csrc/wdlb_shell_tiled.cuh",
               "csrc/wdlb_step_kernels.cuh", "build.py"):
         with open(os.path.join(pkg, f), "rb") as fh:
             h.update(fh.read())
@@ -312,7 +312,7 @@ def cpu_baseline_oracle():
                               "sample": "2 time steps of pore 0 of the batch (%d nodes, %.1f s)" % (done // 2, dt1)}}
 
 
-def run_serving(w, synth, np, rate, window_s, drain_s, max_active=48, tol=1e-8):
+def run_serving(w, synth, np, rate, window_s, drain_s, max_active=48, tol=1e-8, collision="fp32"):
     """Continuous-batching server fed with Poisson arrivals in real time; each
     request runs until the relative change per step of its pore flux is below
     tol.  Requests arrive for window_s seconds, then the server drains for up
@@ -321,7 +321,7 @@ def run_serving(w, synth, np, rate, window_s, drain_s, max_active=48, tol=1e-8):
     reqs = synth.serving_requests(rate, window_s)
     fields = [synth.slit_poiseuille(q["nx"], q["ny"], q["nz"], q["n_star"], q["sigma"], q["tau"], q["gx"], seed)
               for _, q, seed in reqs]
-    srv = w.wdlb_server_create(24 << 30, max_active=max_active, check_every=100)
+    srv = w.wdlb_server_create(24 << 30, max_active=max_active, check_every=100, collision=collision)
     submitted = {}
     t_start = time.perf_counter()
     for (t_arr, q, _), (pp, n, _) in zip(reqs, fields):
@@ -361,7 +361,7 @@ def run_serving(w, synth, np, rate, window_s, drain_s, max_active=48, tol=1e-8):
             "solves_per_s": len(ok) / elapsed, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "backlog_at_end": info["queued"] + info["active"],
             "completed_mlups": node_steps / elapsed / 1e6, "server_mlups": info["node_steps"] / elapsed / 1e6,
-            "max_active": max_active}
+            "max_active": max_active, "collision": collision}
 
 
 SERVE_WORKLOAD = ("slit Poiseuille requests: sigma in {3,4,6}, H/sigma lognormal (median 10, log-sd 0.5) clipped "
@@ -372,28 +372,32 @@ SERVE_WORKLOAD = ("slit Poiseuille requests: sigma in {3,4,6}, H/sigma lognormal
 
 def run_single_pore(w, synth, np, count=2, tol=1e-8):
     """The first `count` requests of the serving stream solved one at a time,
-    alone on the GPU, on the plain FP64 path and on the FP32 path (same
-    kernels as the batch), to the same steady-state tolerance; solves/s of
-    each and the largest relative difference of their pore fluxes."""
+    alone on the GPU, on the plain FP64 path, the FP32 path (same kernels as
+    the batch) and FP32 storage with the double-word collision, to the same
+    steady-state tolerance; solves/s of each and the largest relative
+    difference of each FP32 path's pore fluxes from the FP64 path's."""
     reqs = synth.serving_requests(200.0, 5.0)[:count]
     out = {}
     flux = {}
-    for storage in ("f64", "f32"):
+    for path in ("f64", "f32", "f32_dw"):
+        storage, collision = ("f32", "dw") if path == "f32_dw" else (path, "fp32")
         t_total, steps_total = 0.0, 0
         for k, (_, q, seed) in enumerate(reqs):
             pp, n, _ = synth.slit_poiseuille(q["nx"], q["ny"], q["nz"], q["n_star"], q["sigma"], q["tau"], q["gx"],
                                              seed)
-            ctx = w.wdlb_create((q["nx"], q["ny"], q["nz"]), q["sigma"], True, q["tau"], pp["g"], storage=storage)
+            ctx = w.wdlb_create((q["nx"], q["ny"], q["nz"]), q["sigma"], True, q["tau"], pp["g"], storage=storage,
+                                collision=collision)
             w.wdlb_init_fields(ctx, n)
             t0 = time.perf_counter()
             steps, _ = w.wdlb_run_steady(ctx, tol, 100, 10 ** 6)
             t_total += time.perf_counter() - t0
             steps_total += steps
-            flux[(storage, k)] = w.wdlb_pore_average(ctx)["flux_x"]
+            flux[(path, k)] = w.wdlb_pore_average(ctx)["flux_x"]
             w.wdlb_destroy(ctx)
-        out[storage] = {"solves_per_s": count / t_total, "seconds": t_total, "time_steps": steps_total}
-    out["flux_rel_diff_max"] = max(abs(flux[("f32", k)] - flux[("f64", k)]) / abs(flux[("f64", k)])
-                                   for k in range(count))
+        out[path] = {"solves_per_s": count / t_total, "seconds": t_total, "time_steps": steps_total}
+    for path in ("f32", "f32_dw"):
+        out[path]["flux_rel_diff_max_vs_f64"] = max(abs(flux[(path, k)] - flux[("f64", k)]) / abs(flux[("f64", k)])
+                                                   for k in range(count))
     out["sample"] = ("first %d requests of the serving stream, solved one at a time to relative pore-flux "
                      "change < %g per step" % (count, tol))
     return out
@@ -408,6 +412,9 @@ def run_serving_pair(w, synth, np):
     out = {"workload": SERVE_WORKLOAD, "overload": over, "capacity_solves_per_s": cap}
     if cap > 0:
         out["at_70pct_capacity"] = run_serving(w, synth, np, rate=0.7 * cap, window_s=20.0, drain_s=20.0)
+    # capacity of the served stream with the double-word collision (steady
+    # flows within 1e-5 of the FP64 oracle on u_x and flux)
+    out["overload_dw_collision"] = run_serving(w, synth, np, rate=200.0, window_s=5.0, drain_s=25.0, collision="dw")
     out["single_pore"] = run_single_pore(w, synth, np)
     return out
 
@@ -516,7 +523,8 @@ def run_ours(args):
     w.wdlb_batch_destroy(probe)
     # the built-in tile rule (sigma 4: 8 x 8 x 4 bricks at every pore height)
     # keeps the shell phase one launch for all pores
-    bt = w.wdlb_batch_create(len(pores), pool + (1 << 20), storage="f32", autotune=False)
+    bt = w.wdlb_batch_create(len(pores), pool + (1 << 20), storage="f32", autotune=False,
+                             collision=args.collision if args.only_device else "fp32")
     slots = [w.wdlb_batch_add(bt, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"], pp["tau"], pp["g"], nn, uu)
              for pp, nn, uu in pores]
     tiles = sorted({w.wdlb_tile_info(w.wdlb_batch_context(bt, s)) for s in slots})
@@ -575,31 +583,39 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # ---------------- A/B: the same batch on the persistent dataflow step ----------------
-    bp = w.wdlb_batch_create(len(pores), pool + (1 << 20), storage="f32", autotune=False, persistent=True)
-    pslots = [w.wdlb_batch_add(bp, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"], pp["tau"], pp["g"], nn,
-                               uu) for pp, nn, uu in pores]
-    for _ in range(args.warmup):
-        w.wdlb_batch_step(bp, SUB)
-        w.wdlb_batch_residuals(bp, SUB)
-    pa = torch.cuda.Event(enable_timing=True)
-    pb = torch.cuda.Event(enable_timing=True)
-    pl0 = w.wdlb_batch_launch_count(bp)
-    torch.cuda.synchronize()
-    pa.record(bp.stream)
-    for _ in range(args.steps):
-        w.wdlb_batch_step(bp, SUB)
-        w.wdlb_batch_residuals(bp, SUB)
-    pb.record(bp.stream)
-    torch.cuda.synchronize()
-    _, pst = w.wdlb_batch_residuals(bp, SUB)
-    p_ms = max_over_ranks(pa.elapsed_time(pb))
-    persistent_leg = {"value": job_mlups(world, nodes_b, SUB * args.steps, p_ms * 1e-3), "unit": UNIT,
-                      "ms_per_step": p_ms / args.steps, "gpu_launches": w.wdlb_batch_launch_count(bp) - pl0,
-                      "status_ok": all(int(pst[s]) == 0 for s in pslots),
-                      "form": "one persistent kernel per %d time steps; each pore's phases follow one another "
-                              "without device-wide barriers (value: graph replays of one launch per phase)" % SUB}
-    w.wdlb_batch_destroy(bp)
+    # ---------------- the same batch on other forms of the step ----------------
+    def batch_leg(persistent, collision, form):
+        bp = w.wdlb_batch_create(len(pores), pool + (1 << 20), storage="f32", autotune=False, persistent=persistent,
+                                 collision=collision)
+        pslots = [w.wdlb_batch_add(bp, (pp["nx"], pp["ny"], pp["nz"]), pp["sigma"], pp["walls"], pp["tau"], pp["g"],
+                                   nn, uu) for pp, nn, uu in pores]
+        for _ in range(args.warmup):
+            w.wdlb_batch_step(bp, SUB)
+            w.wdlb_batch_residuals(bp, SUB)
+        pa = torch.cuda.Event(enable_timing=True)
+        pb = torch.cuda.Event(enable_timing=True)
+        pl0 = w.wdlb_batch_launch_count(bp)
+        torch.cuda.synchronize()
+        pa.record(bp.stream)
+        for _ in range(args.steps):
+            w.wdlb_batch_step(bp, SUB)
+            w.wdlb_batch_residuals(bp, SUB)
+        pb.record(bp.stream)
+        torch.cuda.synchronize()
+        _, pst = w.wdlb_batch_residuals(bp, SUB)
+        p_ms = max_over_ranks(pa.elapsed_time(pb))
+        leg = {"value": job_mlups(world, nodes_b, SUB * args.steps, p_ms * 1e-3), "unit": UNIT,
+               "ms_per_step": p_ms / args.steps, "gpu_launches": w.wdlb_batch_launch_count(bp) - pl0,
+               "status_ok": all(int(pst[s]) == 0 for s in pslots), "form": form}
+        w.wdlb_batch_destroy(bp)
+        return leg
+
+    persistent_leg = batch_leg(True, "fp32", "one persistent kernel per %d time steps; each pore's phases follow one "
+                                             "another without device-wide barriers (value: graph replays of one "
+                                             "launch per phase)" % SUB)
+    dw_leg = batch_leg(False, "dw", "double-word collision (WDLB_COLLISION_DW): the collision and the push's "
+                                    "re-encoding in pairs of floats, FP32 storage; steady slit flows within 1e-5 of "
+                                    "the FP64 oracle on u_x and flux (FP32 collision: up to 5.4e-5)")
 
     # ---------------- end to end through the public batch API and host buffers ----------------
     pin = []
@@ -807,7 +823,7 @@ def run_ours(args):
                            "source": "a second pass of the same batch launched phase by phase with CUDA events "
                                      "around each launch (%.2f ms per bench step, against %.2f ms for the graph "
                                      "replays timed for value)" % (instrumented_ms, elapsed_ms / args.steps)},
-            "batched_persistent": persistent_leg,
+            "batched_persistent": persistent_leg, "batched_dw_collision": dw_leg,
             "paths": paths, "serve": serve, "pore_viscosity_sweep": sweep}
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -837,6 +853,8 @@ def main():
                     help="with --workload bulk128: 0 skips the shell sums (profiling the per-node work alone)")
     ap.add_argument("--tile", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="tile shape of the tiled shell kernel (-1: autotuner)")
+    ap.add_argument("--collision", default="fp32", choices=["fp32", "dw"],
+                    help="with --only-device: the collision arithmetic of the 64-pore batch (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
