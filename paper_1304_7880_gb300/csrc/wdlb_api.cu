@@ -288,6 +288,7 @@ void set_params(wdlb_ctx *ctx)
     for (int d = 0; d < 3; d++) dw_split(p.g[d], p.g_dw[d]);
     dw_split(p.omega, p.omega_dw);
     dw_split(p.interactions ? p.k_cross * 4.5 : 0.0, p.ka_dw);
+    set_float_params(p);
     const double s2 = 2.0 * ctx->sigma;
     p.s2 = (std::fabs(s2 - std::round(s2)) < 1e-12) ? (int)std::lround(s2) : 0;
     p.tiled = 0;
@@ -304,6 +305,7 @@ void set_reference(wdlb_ctx *ctx, double n_ref)
     p.n_off = n_ref;
     p.ref_ng = n_ref * contact_g_host(ctx->opt.closure, p.chi_of_n * n_ref);
     p.h_off = 0.5 * p.chi_of_n * p.n_off;
+    set_float_params(p);
 }
 
 void drop_graphs(wdlb_ctx *ctx)

@@ -76,7 +76,38 @@ struct KParams {
     float g_dw[3][2];
     float omega_dw[2];
     float ka_dw[2];
+    // the doubles above rounded to float once (set_float_params), for the
+    // FP32 kernels: a per-thread conversion would run on the FP64 pipe
+    float f_g[3], f_omega, f_tau, f_k_cross, f_n_off, f_sig2, f_beta, f_wshell, f_chi_of_n, f_c_half, f_h_off,
+        f_ref_ng, f_h_pred;
 };
+
+// Fill the float copies of KParams' doubles (after any of them changes).
+inline __host__ __device__ void set_float_params(KParams &p)
+{
+    for (int d = 0; d < 3; d++) p.f_g[d] = float(p.g[d]);
+    p.f_omega = float(p.omega);
+    p.f_tau = float(p.tau);
+    p.f_k_cross = float(p.k_cross);
+    p.f_n_off = float(p.n_off);
+    p.f_sig2 = float(p.sig2);
+    p.f_beta = float(p.beta);
+    p.f_wshell = float(p.wshell);
+    p.f_chi_of_n = float(p.chi_of_n);
+    p.f_c_half = float(p.c_half);
+    p.f_h_off = float(p.h_off);
+    p.f_ref_ng = float(p.ref_ng);
+    p.f_h_pred = float(p.h_pred);
+}
+
+// A parameter in the compute type T: the double itself, or its float copy
+// (the same value a device conversion of the double gives).
+template <class T>
+__device__ __forceinline__ T prm(double d, float f);
+template <>
+__device__ __forceinline__ double prm<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float prm<float>(double, float f) { return f; }
 
 // Tiled ball sum: an 8 x 8 x 8 brick of nodes per block with a halo of
 // ball_r, the brick's n - n_off and the ball's offsets in shared memory.

@@ -1,15 +1,19 @@
 // Double-word arithmetic on the FP32 units ("float-float"): a value is the
-// unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2, about 48
-// significant bits.  Built from the error-free transformations of Knuth's
-// two-sum, Dekker's fast two-sum (|a| >= |b|) and the product error that one
-// fused multiply-add gives exactly; addition is the short ("sloppy") form
-// whose error is bounded relative to the larger operand, which is what a sum
-// that cancels down to a small difference needs here.  Every sum and product
-// is a round-to-nearest intrinsic, so contraction cannot change the
-// error-free steps and a checked build computes the same bits.
+// unevaluated sum hi + lo of two floats, about 48 significant bits.  Built
+// from the error-free transformations of Knuth's two-sum, Dekker's fast
+// two-sum (|a| >= |b|) and the product error that one fused multiply-add
+// gives exactly.  Results are left unnormalised (|lo| may exceed ulp(hi)/2
+// by a few ulps of lo): the next two-sum takes hi exactly and the final
+// rounding (dw_round) adds lo back, so the pair keeps ~2^-44 of the larger
+// operand, while skipping the fast two-sum after every operation saves three
+// instructions each.  Addition is the short form, whose error is bounded
+// relative to the larger operand: what a sum that cancels down to a small
+// difference needs here.  Every sum and product is a round-to-nearest
+// intrinsic, so contraction cannot change the error-free steps and a checked
+// build computes the same bits.
 //
-// GB300 issues FP64 at 1/64 of its FP32 rate; each operation below costs 3 to
-// 11 FP32 instructions.
+// GB300 issues FP64 at 1/64 of its FP32 rate; each operation below costs 2 to
+// 8 FP32 instructions (the division 12).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -69,13 +73,13 @@ __device__ __forceinline__ dwf operator-(dwf a) { return dwf{-a.hi, -a.lo}; }
 __device__ __forceinline__ dwf operator+(dwf a, dwf b)
 {
     const dwf s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+    return dwf{s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
 }
 
 __device__ __forceinline__ dwf operator+(dwf a, float b)
 {
     const dwf s = two_sum(a.hi, b);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+    return dwf{s.hi, __fadd_rn(s.lo, a.lo)};
 }
 
 __device__ __forceinline__ dwf operator+(float a, dwf b) { return b + a; }
@@ -88,15 +92,17 @@ __device__ __forceinline__ dwf operator*(dwf a, dwf b)
     const float p = __fmul_rn(a.hi, b.hi);
     const float e = __fmaf_rn(a.hi, b.hi, -p);
     const float t = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
-    return fast_two_sum(p, __fadd_rn(e, t));
+    return dwf{p, __fadd_rn(e, t)};
 }
 
 __device__ __forceinline__ dwf operator*(dwf a, float b)
 {
     const float p = __fmul_rn(a.hi, b);
-    const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
-    return fast_two_sum(p, e);
+    return dwf{p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p))};
 }
+
+// a times a power of two (exact, away from underflow)
+__device__ __forceinline__ dwf dw_scale2(dwf a, float s) { return dwf{__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)}; }
 
 __device__ __forceinline__ dwf operator*(float a, dwf b) { return b * a; }
 
@@ -107,12 +113,13 @@ __device__ __forceinline__ dwf two_prod(float a, float b)
     return dwf{p, __fmaf_rn(a, b, -p)};
 }
 
-// a / b: one correction of the float quotient
+// a / b: one correction of the float quotient (the remainder's two parts
+// added first: unnormalised, its hi need not lead)
 __device__ __forceinline__ dwf operator/(dwf a, dwf b)
 {
     const float q1 = __fdiv_rn(a.hi, b.hi);
     const dwf r = a - b * q1;
-    return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+    return fast_two_sum(q1, __fdiv_rn(__fadd_rn(r.hi, r.lo), b.hi));
 }
 
 __device__ __forceinline__ dwf &operator+=(dwf &a, dwf b) { return a = a + b; }

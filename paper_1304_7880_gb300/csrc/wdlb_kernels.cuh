@@ -63,14 +63,14 @@ __global__ void __launch_bounds__(256) k_init(KParams p, KBufs<S, typename Store
     int z = i / (p.nx * p.ny);
     bool solid = solid_plane(p, z);
     // deviations from n_off are formed in FP64 before rounding to T
-    const T dnv = solid ? -T(p.n_off) : T(st_n[i] - p.n_off);
-    T n = solid ? T(0) : T(p.n_off) + dnv;
+    const T dnv = solid ? -prm<T>(p.n_off, p.f_n_off) : T(st_n[i] - p.n_off);
+    T n = solid ? T(0) : prm<T>(p.n_off, p.f_n_off) + dnv;
     T ux = solid || !st_u ? T(0) : T(st_u[i]);
     T uy = solid || !st_u ? T(0) : T(st_u[p.N + i]);
     T uz = solid || !st_u ? T(0) : T(st_u[2 * p.N + i]);
     // local rest state s(r) = n (solid nodes: n_off, their slots are never read)
     const T dsc = solid ? T(0) : dnv;
-    const T sc = T(p.n_off) + dsc;
+    const T sc = prm<T>(p.n_off, p.f_n_off) + dsc;
     const T uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
@@ -103,11 +103,11 @@ __device__ __forceinline__ void moments_body(const KParams &p, const KBufs<S, ty
             if (out_n) out_n[i] = 0.0;
             if (out_u) out_u[i] = out_u[p.N + i] = out_u[2 * p.N + i] = 0.0;
         } else {
-            b.nu[i] = V4<T>{-T(p.n_off), T(0), T(0), T(0)};
+            b.nu[i] = V4<T>{-prm<T>(p.n_off, p.f_n_off), T(0), T(0), T(0)};
         }
         return;
     }
-    const T noff = T(p.n_off);
+    const T noff = prm<T>(p.n_off, p.f_n_off);
     const T dsc = b.nscale[i];
     const T sc = noff + dsc;
     T dl = T(0), jx = T(0), jy = T(0), jz = T(0);
@@ -124,13 +124,13 @@ __device__ __forceinline__ void moments_body(const KParams &p, const KBufs<S, ty
     if (!(n > T(0)) || !isfinite(n)) atomicOr(b.status, 1);
     const T inv = T(1) / n;
     const V4<T> old = b.nu[i];
-    const T H = T(p.h_pred) * b.tprev[i];
+    const T H = prm<T>(p.h_pred, p.f_h_pred) * b.tprev[i];
     const T den = T(1) / (T(1) + H);
     // every multiply-add written out, so each kernel that runs this body
     // (the per-phase step and the persistent one) computes the same bits
-    const T vx = fma(H, old.y, fma(T(0.5), fma(n, T(p.g[0]), b.cprev[i]), jx) * inv) * den;
-    const T vy = fma(H, old.z, fma(T(0.5), fma(n, T(p.g[1]), b.cprev[p.Npad + i]), jy) * inv) * den;
-    const T vz = fma(H, old.w, fma(T(0.5), fma(n, T(p.g[2]), b.cprev[2 * p.Npad + i]), jz) * inv) * den;
+    const T vx = fma(H, old.y, fma(T(0.5), fma(n, prm<T>(p.g[0], p.f_g[0]), b.cprev[i]), jx) * inv) * den;
+    const T vy = fma(H, old.z, fma(T(0.5), fma(n, prm<T>(p.g[1], p.f_g[1]), b.cprev[p.Npad + i]), jy) * inv) * den;
+    const T vz = fma(H, old.w, fma(T(0.5), fma(n, prm<T>(p.g[2], p.f_g[2]), b.cprev[2 * p.Npad + i]), jz) * inv) * den;
     if (OUT) {
         if (out_n) out_n[i] = double(n);
         if (out_u) {
@@ -164,10 +164,10 @@ __device__ __forceinline__ void ball_body(const KParams &p, const V4<T> *nu, T *
     int y = (i / p.nx) % p.ny;
     int z = i / (p.nx * p.ny);
     if (solid_plane(p, z)) {
-        hb[i] = -T(p.h_off);    // n = 0: chi = 0
+        hb[i] = -prm<T>(p.h_off, p.f_h_off);    // n = 0: chi = 0
         return;
     }
-    const T noff = T(p.n_off);
+    const T noff = prm<T>(p.n_off, p.f_n_off);
     T sum = T(0);               // sum over the ball of n - n_off
     for (int m = 0; m < p.nball; m++) {
         int4 e = ball[m];
@@ -185,8 +185,8 @@ __device__ __forceinline__ void ball_body(const KParams &p, const V4<T> *nu, T *
         const int j = xx + p.nx * (yy + p.ny * zz);
         if (in_bounds(j, p.N, status)) sum += nu[j].x;
     }
-    T dh = T(p.c_half) * sum;
-    if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
+    T dh = prm<T>(p.c_half, p.f_c_half) * sum;
+    if (!(prm<T>(p.h_off, p.f_h_off) + dh < T(0.5))) atomicOr(status, 1);
     hb[i] = dh;
 }
 
@@ -208,7 +208,7 @@ __device__ __forceinline__ void ball_tiled_body(const KParams &p, const V4<T> *n
         const int4 e = ball[m];
         so[m] = e.x + SX * (e.y + SX * e.z);
     }
-    const T noff = T(p.n_off);
+    const T noff = prm<T>(p.n_off, p.f_n_off);
     const int x0 = bx * kBallTile, y0 = by * kBallTile, z0 = bz * kBallTile;
     for (int idx = threadIdx.x; idx < NS; idx += blockDim.x) {
         const int sx = idx % SX, sy = (idx / SX) % SX, sz = idx / (SX * SX);
@@ -234,15 +234,15 @@ __device__ __forceinline__ void ball_tiled_body(const KParams &p, const V4<T> *n
         if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
         const int i = x + p.nx * (y + p.ny * z);
         if (solid_plane(p, z)) {
-            hb[i] = -T(p.h_off);
+            hb[i] = -prm<T>(p.h_off, p.f_h_off);
             continue;
         }
         const int base = (tx + R) + SX * ((ty + R) + SX * (tz + R));
         T sum = T(0);
         for (int m = 0; m < p.nball; m++)
             if (in_bounds(base + so[m], NS, status)) sum += sn[base + so[m]];
-        T dh = T(p.c_half) * sum;
-        if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
+        T dh = prm<T>(p.c_half, p.f_c_half) * sum;
+        if (!(prm<T>(p.h_off, p.f_h_off) + dh < T(0.5))) atomicOr(status, 1);
         hb[i] = dh;
     }
 }
@@ -259,7 +259,7 @@ __device__ __forceinline__ void ball_brick_ct(const KParams &p, const V4<T> *nu,
     constexpr int SX = kBallTile + 2 * R, NS = SX * SX * SX;
     extern __shared__ __align__(16) unsigned char ball_smem[];
     T *sn = reinterpret_cast<T *>(ball_smem);
-    const T noff = T(p.n_off);
+    const T noff = prm<T>(p.n_off, p.f_n_off);
     const int x0 = bx * kBallTile, y0 = by * kBallTile, z0 = bz * kBallTile;
     for (int idx = threadIdx.x; idx < NS; idx += blockDim.x) {
         const int sx = idx % SX, sy = (idx / SX) % SX, sz = idx / (SX * SX);
@@ -285,7 +285,7 @@ __device__ __forceinline__ void ball_brick_ct(const KParams &p, const V4<T> *nu,
         if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
         const int i = x + p.nx * (y + p.ny * z);
         if (solid_plane(p, z)) {
-            hb[i] = -T(p.h_off);
+            hb[i] = -prm<T>(p.h_off, p.f_h_off);
             continue;
         }
         const T *c = sn + (tx + R) + SX * ((ty + R) + SX * (tz + R));
@@ -299,8 +299,8 @@ __device__ __forceinline__ void ball_brick_ct(const KParams &p, const V4<T> *nu,
                     if (16 * (dx * dx + dy * dy + dz * dz) <= S2 * S2 &&
                         in_bounds(c - sn + dx + SX * (dy + SX * dz), NS, status))
                         sum += c[dx + SX * (dy + SX * dz)];
-        T dh = T(p.c_half) * sum;
-        if (!(T(p.h_off) + dh < T(0.5))) atomicOr(status, 1);
+        T dh = prm<T>(p.c_half, p.f_c_half) * sum;
+        if (!(prm<T>(p.h_off, p.f_h_off) + dh < T(0.5))) atomicOr(status, 1);
         hb[i] = dh;
     }
 }
@@ -420,15 +420,15 @@ template <class T>
 __device__ __forceinline__ void shell_forces(const KParams &p, const ShellAcc<T> &a, T n, T vx, T vy, T vz, T &Cx,
                                              T &Cy, T &Cz, T &Axx, T &Ayy, T &Azz, T &Axy, T &Axz, T &Ayz, T &tsum)
 {
-    const T wh = T(0.5) * T(p.wshell);
-    const T mf = -T(CS2) * T(p.sig2) * wh * n;
-    const T vi = T(p.beta) * wh * n;
+    const T wh = T(0.5) * prm<T>(p.wshell, p.f_wshell);
+    const T mf = -T(CS2) * prm<T>(p.sig2, p.f_sig2) * wh * n;
+    const T vi = prm<T>(p.beta, p.f_beta) * wh * n;
     // multiply-adds written out (the same bits in every kernel); the product
     // with the mean-field sum V, the larger term next to a wall, enters exactly
     Cx = fma(mf, a.Vx, vi * a.Wx);
     Cy = fma(mf, a.Vy, vi * a.Wy);
     Cz = fma(mf, a.Vz, vi * a.Wz);
-    const T pa = -(T(CS2) / T(5)) * T(p.sig2) * n * wh;
+    const T pa = -(T(CS2) / T(5)) * prm<T>(p.sig2, p.f_sig2) * n * wh;
     Axx = T(2) * pa * fma(-a.Vx, vx, a.Sxx);
     Ayy = T(2) * pa * fma(-a.Vy, vy, a.Syy);
     Azz = T(2) * pa * fma(-a.Vz, vz, a.Szz);
@@ -452,7 +452,7 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
                                              T tsum, T dn_self, TargetDn target_dn)
 {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const T noff = T(p.n_off);
+    const T noff = prm<T>(p.n_off, p.f_n_off);
     const T dsc = b.nscale[i];           // this node's storage scale - n_off
     const T sc = noff + dsc;
     T d[NQ];
@@ -469,7 +469,7 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
     const T inv_n = T(1) / n;
 
     // collision velocity u = (j + F/2)/n with F = n g + C
-    const T Fx = n * T(p.g[0]) + Cx, Fy = n * T(p.g[1]) + Cy, Fz = n * T(p.g[2]) + Cz;
+    const T Fx = n * prm<T>(p.g[0], p.f_g[0]) + Cx, Fy = n * prm<T>(p.g[1], p.f_g[1]) + Cy, Fz = n * prm<T>(p.g[2], p.f_g[2]) + Cz;
     const T ux = (jx + T(0.5) * Fx) * inv_n;
     const T uy = (jy + T(0.5) * Fy) * inv_n;
     const T uz = (jz + T(0.5) * Fz) * inv_n;
@@ -485,11 +485,11 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
     }
 
     // relaxation frequency
-    T omega = T(p.omega);
+    T omega = prm<T>(p.omega, p.f_omega);
     if (p.omega_mode == 1) {
         const T chib = T(2) * hr;
-        const T loc = chib / T(p.chi_of_n) * contact_g<CL, T>(chib);
-        T tau = loc > T(0) ? T(0.5) + (T(p.tau) - T(0.5)) * T(p.ref_ng) / loc : T(1e30);
+        const T loc = chib / prm<T>(p.chi_of_n, p.f_chi_of_n) * contact_g<CL, T>(chib);
+        T tau = loc > T(0) ? T(0.5) + (prm<T>(p.tau, p.f_tau) - T(0.5)) * prm<T>(p.ref_ng, p.f_ref_ng) / loc : T(1e30);
         tau = tau < T(0.501) ? T(0.501) : tau;
         omega = T(1) / tau;
     }
@@ -497,7 +497,7 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
     // collision (Eq. SMDB, second order): f* = f - omega (f - feq) + (1 - omega/2)(Phi + S^A)
     const T tr3 = (Axx + Ayy + Azz) * T(1.0 / 3.0);
     const T Bxx = Axx - tr3, Byy = Ayy - tr3, Bzz = Azz - tr3;   // traceless A
-    const T kA = p.interactions ? T(p.k_cross) * T(4.5) : T(0);  // K / (2 c_s^4)
+    const T kA = p.interactions ? prm<T>(p.k_cross, p.f_k_cross) * T(4.5) : T(0);  // K / (2 c_s^4)
     const T uu = ux * ux + uy * uy + uz * uz;
     const T uF = ux * Fx + uy * Fy + uz * Fz;
     const T src_pref = T(1) - T(0.5) * omega;
@@ -588,7 +588,7 @@ __device__ __forceinline__ void collide_push_dw(const KParams &p, const KBufs<S,
 {
     static_assert(sizeof(S) == sizeof(float), "double-word collision: FP32 storage");
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const float noff = float(p.n_off);
+    const float noff = p.f_n_off;
     const float dsc = b.nscale[i];
     float d[NQ];
     dwf dn = dw_from(0.f), jx = dw_from(0.f), jy = dw_from(0.f), jz = dw_from(0.f);
@@ -605,15 +605,15 @@ __device__ __forceinline__ void collide_push_dw(const KParams &p, const KBufs<S,
 
     // collision velocity u = (j + F/2)/n with F = n g + C
     const dwf Fx = n * dw_load(p.g_dw[0]) + Cx, Fy = n * dw_load(p.g_dw[1]) + Cy, Fz = n * dw_load(p.g_dw[2]) + Cz;
-    const dwf ux = (jx + Fx * 0.5f) * inv_n;
-    const dwf uy = (jy + Fy * 0.5f) * inv_n;
-    const dwf uz = (jz + Fz * 0.5f) * inv_n;
+    const dwf ux = (jx + dw_scale2(Fx, 0.5f)) * inv_n;
+    const dwf uy = (jy + dw_scale2(Fy, 0.5f)) * inv_n;
+    const dwf uz = (jz + dw_scale2(Fz, 0.5f)) * inv_n;
 
     dwf omega = dw_load(p.omega_dw);
     if (p.omega_mode == 1) {
         const float chib = 2.f * hr;
-        const float loc = chib / float(p.chi_of_n) * contact_g<CL, float>(chib);
-        float tau = loc > 0.f ? 0.5f + (float(p.tau) - 0.5f) * float(p.ref_ng) / loc : 1e30f;
+        const float loc = chib / p.f_chi_of_n * contact_g<CL, float>(chib);
+        float tau = loc > 0.f ? 0.5f + (p.f_tau - 0.5f) * p.f_ref_ng / loc : 1e30f;
         tau = tau < 0.501f ? 0.501f : tau;
         omega = dw_from(1.f) / dw_from(tau);
     }
@@ -623,7 +623,7 @@ __device__ __forceinline__ void collide_push_dw(const KParams &p, const KBufs<S,
     const dwf kA = dw_load(p.ka_dw);                               // K / (2 c_s^4), 0 without fields
     const dwf uu15 = (ux * ux + uy * uy + uz * uz) * 1.5f;
     const dwf uF = ux * Fx + uy * Fy + uz * Fz;
-    const dwf src_pref = dw_from(1.f) - omega * 0.5f;
+    const dwf src_pref = dw_from(1.f) - dw_scale2(omega, 0.5f);
     const int nxy = nx * ny;
     const bool inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && (WALLS || (z > 0 && z < nz - 1));
 
@@ -635,10 +635,10 @@ __device__ __forceinline__ void collide_push_dw(const KParams &p, const KBufs<S,
         const dwf cF = dw_cdot(cxq, cyq, czq, Fx, Fy, Fz);
         const dwf feq_dev = wq * (dn + n * (cu * 3.f + (cu * cu) * 4.5f - uu15));
         const dwf phi = wq * ((cF - uF) * 3.f + (cu * cF) * 9.f);
-        dwf cAc = dw_from(0.f);
-        if (cxq) cAc = cAc + Bxx;
-        if (cyq) cAc = cAc + Byy;
-        if (czq) cAc = cAc + Bzz;
+        // c_q^2-weighted diagonal of traceless A (the rest direction has none)
+        dwf cAc = cxq ? Bxx : (cyq ? Byy : (czq ? Bzz : dw_from(0.f)));
+        if (cxq && cyq) cAc = cAc + Byy;
+        if ((cxq || cyq) && czq) cAc = cAc + Bzz;
         if (cxq && cyq) cAc = cAc + float(2 * cxq * cyq) * Axy;
         if (cxq && czq) cAc = cAc + float(2 * cxq * czq) * Axz;
         if (cyq && czq) cAc = cAc + float(2 * cyq * czq) * Ayz;
@@ -686,7 +686,7 @@ __device__ __forceinline__ void shell_sums_generic(const KParams &p, const V4<T>
                                                    T hr, T vx, T vy, T vz, ShellAcc<T> &a, int *status)
 {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const T noff = T(p.n_off), hoff = T(p.h_off);
+    const T noff = prm<T>(p.n_off, p.f_n_off), hoff = prm<T>(p.h_off, p.f_h_off);
     const T s0 = T(1) - hr - hoff;
     auto fetch = [&](int ex, int ey, int ez, V4<T> &nb, T &hbv) {
         int zz = z + ez;
@@ -739,7 +739,7 @@ __device__ __forceinline__ void shell_body(const KParams &p, const KBufs<S, type
     int z = i / (nx * ny);
     if (WALLS && (z == 0 || z == nz - 1)) return;
 
-    const T noff = T(p.n_off), hoff = T(p.h_off);
+    const T noff = prm<T>(p.n_off, p.f_n_off), hoff = prm<T>(p.h_off, p.f_h_off);
     const T dhr = b.hb[i];
     const T hr = hoff + dhr;
     const V4<T> me = b.nu[i];
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(256) k_pop_to_f64(KParams p, const S *f, const
         out[i] = 0.0;
         return;
     }
-    const T sc = T(p.n_off) + nscale[i];
+    const T sc = prm<T>(p.n_off, p.f_n_off) + nscale[i];
     T dv = Store<S>::load(f + (size_t)q * p.Npad + i, T(w_of(q)) * sc);
     out[i] = double(dv) + w_of(q) * double(sc);
 }

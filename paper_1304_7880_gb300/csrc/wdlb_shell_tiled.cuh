@@ -294,7 +294,7 @@ __device__ __forceinline__ void tiled_body(const KParams &p, const KBufs<S, floa
     }
     // the field tile with its halo: one TMA box per array where the tile needs
     // no periodic wrap in x and y (and z without walls), else per-node copies
-    const float noff = float(p.n_off), hoff = float(p.h_off);
+    const float noff = p.f_n_off, hoff = p.f_h_off;
     bool use_tma = false;
     if constexpr (tma_staging<S2>()) {
         // (TMA writes shared memory at 128-byte aligned addresses only)

@@ -69,6 +69,7 @@ __device__ __forceinline__ KParams with_reference(KParams p, const double *ref)
 {
     p.n_off = *ref;
     p.h_off = 0.5 * p.chi_of_n * p.n_off;
+    set_float_params(p);
     return p;
 }
 
@@ -239,6 +240,7 @@ extern "C" wdlb_status wdlb_fields_static(wdlb_lattice lat, double sigma, int32_
     p.wshell = wshell;
     p.chi_of_n = M_PI * sigma * sigma * sigma / 6.0;
     p.c_half = p.chi_of_n / (2.0 * nball);
+    set_float_params(p);
 
     const int blocks = (int)((N + 255) / 256);
     k_static_reference<<<1, 1024, 0, st>>>(p, d_n, s.ref);
