@@ -59,6 +59,7 @@ def _load():
     lib.wo_step.restype = I
     lib.wo_moments.argtypes = [P, P, P]
     lib.wo_fields.argtypes = [P, P, P, P]
+    lib.wo_thermal_fields.argtypes = [P, P, P, P, P]
     lib.wo_get_populations.argtypes = [P, P]
     lib.wo_set_populations.argtypes = [P, P]
     lib.wo_get_cprev.argtypes = [P, P]
@@ -199,6 +200,17 @@ class Oracle:
         A = np.zeros((6,) + self.shape)
         self.lib.wo_fields(self.h, _ptr(nbar), _ptr(C), _ptr(A))
         return nbar, C, A
+
+    def thermal_fields(self, T):
+        """Energy-equation fields of Sec. 3 on a prescribed temperature field T
+        (k_B T per node, lattice units): Q (Eq. campob1), B (Eq. campos) and
+        the thermal force F^T (Eq. thermalforce), on the current populations."""
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(self.shape)
+        Qf = np.zeros(self.shape)
+        B = np.zeros((3,) + self.shape)
+        FT = np.zeros((3,) + self.shape)
+        self.lib.wo_thermal_fields(self.h, _ptr(T), _ptr(Qf), _ptr(B), _ptr(FT))
+        return Qf, B, FT
 
     def populations(self) -> np.ndarray:
         f = np.zeros((19,) + self.shape)

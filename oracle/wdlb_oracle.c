@@ -697,6 +697,53 @@ void wo_fields(wo_state *s, double *nbar_out, double *C_out, double *A_out)
     if (A_out) memcpy(A_out, s->A, sizeof(double) * 6 * N);
 }
 
+/* Energy-equation fields of Sec. 3 on a prescribed temperature field T
+ * (k_B T per node in lattice units, m = 1; solid nodes ignored), evaluated on
+ * the current populations with the same quadrature (R4, R4c), contact values
+ * (R2) and field velocity v (R7) as C and A:
+ *   Q(r)   = T n sigma^2 sum_e w g2 n(r+e) [-khat.(v(r+e)-v(r))/2
+ *                                           + sqrt(T/pi) (T(r+e)-T(r))/T]     (Eq. campob1)
+ *   B_i(r) = -2 T n sigma^2 sum_e w khat_i g2 n(r+e) (T(r+e)-T(r))           (Eq. campos)
+ *   F^T_i(r) = -(sigma^2/2) sum_e w khat_i g2 n(r+e) (T(r+e)-T(r))           (Eq. thermalforce)
+ * with T, n, sigma^2 prefactors at r.  Sec. 5 evolves no temperature (the
+ * paper's runs are isothermal); these are the fields of its energy equation
+ * on a given T.  Outputs are zero on solid nodes. */
+void wo_thermal_fields(wo_state *s, const double *T, double *Q_out, double *B_out, double *FT_out)
+{
+    long N = s->N;
+    double sig2 = s->sigma * s->sigma;
+    double chi_of_n = M_PI * s->sigma * s->sigma * s->sigma / 6.0;
+    moments(s);
+    smeared_density(s);
+    for (int z = 0; z < s->nz; z++)
+        for (int y = 0; y < s->ny; y++)
+            for (int x = 0; x < s->nx; x++) {
+                long i = x + (long)s->nx * (y + (long)s->ny * z);
+                double q = 0.0, b[3] = {0, 0, 0};
+                if (!is_wall(s, z) && s->interactions) {
+                    for (int m = 0; m < s->nshell; m++) {
+                        int ex = s->shell[3 * m], ey = s->shell[3 * m + 1], ez = s->shell[3 * m + 2];
+                        long k = neighbour(s, x, y, z, ex, ey, ez);
+                        if (k < 0 || is_wall(s, z + ez)) continue;
+                        double len = sqrt((double)(ex * ex + ey * ey + ez * ez));
+                        double kh[3] = {ex / len, ey / len, ez / len};
+                        double chi = chi_of_n * 0.5 * (s->nbar[i] + s->nbar[k]);
+                        double wgn = s->wvec[m] * wo_closure(s->closure, chi) * s->n[k];
+                        double dT = T[k] - T[i];
+                        double kdu = 0.0;
+                        for (int d = 0; d < 3; d++) kdu += kh[d] * (s->us[d * N + k] - s->us[d * N + i]);
+                        q += wgn * (-0.5 * kdu + sqrt(T[i] / M_PI) * dT / T[i]);
+                        for (int d = 0; d < 3; d++) b[d] += wgn * kh[d] * dT;
+                    }
+                }
+                if (Q_out) Q_out[i] = is_wall(s, z) ? 0.0 : T[i] * s->n[i] * sig2 * q;
+                for (int d = 0; d < 3; d++) {
+                    if (B_out) B_out[d * N + i] = is_wall(s, z) ? 0.0 : -2.0 * T[i] * s->n[i] * sig2 * b[d];
+                    if (FT_out) FT_out[d * N + i] = is_wall(s, z) ? 0.0 : -0.5 * sig2 * b[d];
+                }
+            }
+}
+
 void wo_get_populations(const wo_state *s, double *f_out)
 {
     memcpy(f_out, s->f, sizeof(double) * Q * s->N);
