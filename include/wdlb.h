@@ -220,6 +220,24 @@ wdlb_status wdlb_moments_device(wdlb_ctx *ctx, double *d_n, double *d_u);
  * allocates temporary device memory for its FP64 outputs. */
 wdlb_status wdlb_fields(wdlb_ctx *ctx, double *nbar, double *C, double *A, double *u);
 
+/* Energy-equation fields of Sec. 3 on a prescribed temperature field, from
+ * the current state (its n, field velocity v and smeared density, with the
+ * shell quadrature and contact values of C and A):
+ *   Q    (N)  = T n sigma^2 sum_e w g2 n(r+e) [-khat.(v(r+e)-v(r))/2
+ *                                             + sqrt(T/pi) (T(r+e)-T(r))/T]   (Eq. campob1)
+ *   B    (3N) = -2 T n sigma^2 sum_e w khat g2 n(r+e) (T(r+e)-T(r))           (Eq. campos)
+ *   FT   (3N) = -(sigma^2/2) sum_e w khat g2 n(r+e) (T(r+e)-T(r))             (Eq. thermalforce)
+ * T: N doubles on the host, k_B T per node in lattice units (m = 1), finite
+ * and positive on fluid nodes (values on solid planes are ignored); outputs
+ * are host arrays (any may be NULL), zero on solid nodes, computed in FP64
+ * from the state's storage precision.  The time step itself is isothermal
+ * (Sec. 5: k_B T = 1/3 in C and A) and no temperature is evolved; this
+ * evaluates the fields of the paper's energy equation on a given T.  Does not
+ * advance the state.  Synchronous; allocates temporary device memory.
+ * WDLB_ERR_ARG on a NULL T or a non-positive or non-finite T on a fluid node;
+ * WDLB_ERR_STATE before init. */
+wdlb_status wdlb_thermal_fields(wdlb_ctx *ctx, const double *T, double *Q, double *B, double *FT);
+
 /* Populations f_q of the current state as FP64 (19N doubles, q-major, in the
  * order of wdlb_velocity_set), solid nodes 0.  Synchronous. */
 wdlb_status wdlb_get_populations(wdlb_ctx *ctx, double *f);

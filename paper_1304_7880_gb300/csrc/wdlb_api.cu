@@ -810,6 +810,40 @@ wdlb_status wdlb_fields(wdlb_ctx *ctx, double *nbar, double *C, double *A, doubl
     return check_status_word(ctx);
 }
 
+wdlb_status wdlb_thermal_fields(wdlb_ctx *ctx, const double *T, double *Q, double *B, double *FT)
+{
+    if (!ctx) return WDLB_ERR_ARG;
+    if (!T) return fail(ctx, WDLB_ERR_ARG, "T is NULL");
+    if (!ctx->initialised) return fail(ctx, WDLB_ERR_STATE, "thermal fields before init");
+    const size_t N = ctx->N;
+    const int nxy = ctx->lat.nx * ctx->lat.ny;
+    for (size_t i = 0; i < N; i++) {
+        const int z = (int)(i / nxy);
+        const bool solid = ctx->walls && (z == 0 || z == ctx->lat.nz - 1);
+        if (!solid && !(std::isfinite(T[i]) && T[i] > 0.0))
+            return fail(ctx, WDLB_ERR_ARG, "T must be finite and positive on fluid nodes (node %zu)", i);
+    }
+    // temporary FP64 arrays (an inspection path; the time step never allocates)
+    double *buf = nullptr;
+    const size_t nu_bytes = ctx->lay.hb - ctx->lay.nu;   // the field array is overwritten by the moments pass
+    WDLB_CUDA(ctx, cudaMalloc(&buf, 8 * N * sizeof(double) + nu_bytes));
+    double *dT = buf, *dQ = buf + N, *dB = buf + 2 * N, *dF = buf + 5 * N;
+    char *save = reinterpret_cast<char *>(buf + 8 * N);
+    cudaError_t e = cudaMemcpyAsync(save, ctx->dev.nu, nu_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dT, T, N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    for (int part = 0; part < 2 && e == cudaSuccess; part++)
+        e = ctx->L->batch_step(ctx->launch, ctx->cur, part, -1, ctx->stream, &ctx->launches);
+    if (e == cudaSuccess) e = ctx->L->thermal(ctx->kp, ctx->dev, ctx->cur, dT, dQ, dB, dF, ctx->stream, &ctx->launches);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->dev.nu, save, nu_bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess && Q) e = cudaMemcpyAsync(Q, dQ, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && B) e = cudaMemcpyAsync(B, dB, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && FT) e = cudaMemcpyAsync(FT, dF, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "thermal fields");
+    return check_status_word(ctx);
+}
+
 wdlb_status wdlb_get_populations(wdlb_ctx *ctx, double *f)
 {
     if (!ctx || !f) return ctx ? fail(ctx, WDLB_ERR_ARG, "f is NULL") : WDLB_ERR_ARG;

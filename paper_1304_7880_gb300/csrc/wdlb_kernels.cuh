@@ -771,6 +771,73 @@ __global__ void __launch_bounds__(256) k_shell_collide(KParams p, KBufs<S, typen
 }
 
 // ---------------------------------------------------------------------------
+// Energy-equation fields of Sec. 3 on a prescribed temperature T (k_B T per
+// node, lattice units, m = 1), in FP64 from the state's fields (n, the field
+// velocity v, the smeared density) with the shell sum of C and A:
+//   Q    = T n sigma^2 sum_e w g2 n(r+e) [-khat.(v(r+e) - v(r))/2
+//                                         + sqrt(T/pi) (T(r+e) - T(r))/T]   (Eq. campob1)
+//   B_i  = -2 T n sigma^2 sum_e w khat_i g2 n(r+e) (T(r+e) - T(r))           (Eq. campos)
+//   F^T_i = -(sigma^2/2) sum_e w khat_i g2 n(r+e) (T(r+e) - T(r))            (Eq. thermalforce)
+// g2 at the mean of the two ends' smeared densities; khat = e/|e| in FP64;
+// w the uniform shell weight or, with the compact rule, the vector's own.
+// Zero on solid nodes.  An inspection path: the time step is isothermal
+// (Sec. 5) and never runs it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double g2_contact_f64(int closure, double chi)
+{
+    if (closure == 0) return (1.0 - 0.5 * chi) / ((1.0 - chi) * (1.0 - chi) * (1.0 - chi));
+    if (closure == 1) return (1.0 + 0.5 * chi) / ((1.0 - chi) * (1.0 - chi));
+    return 1.0;
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_thermal_fields(KParams p, KBufs<S, typename Store<S>::T> b, const double *T,
+                                                        double *Qo, double *Bo, double *Fo)
+{
+    typedef typename Store<S>::T Tc;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    const int nx = p.nx, ny = p.ny, nz = p.nz, N = p.N;
+    const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+    double q = 0.0, bs[3] = {0.0, 0.0, 0.0};
+    const bool solid = solid_plane(p, z);
+    const V4<Tc> me = b.nu[i];
+    const double ni = p.n_off + double(me.x), Ti = T[i];
+    if (!solid && p.interactions) {
+        const double hr = p.h_off + double(b.hb[i]);
+        for (int m = 0; m < p.nshell; m++) {
+            const int4 e = b.shell_e[m];
+            int zz = z + e.z;
+            if (p.walls) {
+                if (zz <= 0 || zz >= nz - 1) continue;     // beyond or on a wall: n = 0
+            } else {
+                zz = wrap_coord(zz, nz);
+            }
+            const int j = wrap_coord(x + e.x, nx) + nx * (wrap_coord(y + e.y, ny) + ny * zz);
+            if (!in_bounds(j, N, b.status)) continue;
+            const V4<Tc> nb = b.nu[j];
+            const double len = sqrt(double(e.x * e.x + e.y * e.y + e.z * e.z));
+            const double kx = e.x / len, ky = e.y / len, kz = e.z / len;
+            const double chi = hr + p.h_off + double(b.hb[j]);    // chi_mid = h(r) + h(r+e), h = chi/2
+            const double w = p.shell_rule ? double(b.shell_k[m].w) : p.wshell;
+            const double wgn = w * g2_contact_f64(p.closure, chi) * (p.n_off + double(nb.x));
+            const double dT = T[j] - Ti;
+            const double kdu = kx * (double(nb.y) - double(me.y)) + ky * (double(nb.z) - double(me.z)) +
+                               kz * (double(nb.w) - double(me.w));
+            q += wgn * (-0.5 * kdu + sqrt(Ti / M_PI) * dT / Ti);
+            bs[0] += wgn * kx * dT;
+            bs[1] += wgn * ky * dT;
+            bs[2] += wgn * kz * dT;
+        }
+    }
+    Qo[i] = solid ? 0.0 : Ti * ni * p.sig2 * q;
+    for (int d = 0; d < 3; d++) {
+        Bo[d * N + i] = solid ? 0.0 : -2.0 * Ti * ni * p.sig2 * bs[d];
+        Fo[d * N + i] = solid ? 0.0 : -0.5 * p.sig2 * bs[d];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Outputs and FP64 reductions.
 // ---------------------------------------------------------------------------
 template <class S>

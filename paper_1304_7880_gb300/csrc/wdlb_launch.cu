@@ -207,6 +207,14 @@ cudaError_t do_init(const KParams &p, const DevBufs &d, int cur, const double *d
     return cudaGetLastError();
 }
 
+cudaError_t do_thermal(const KParams &p, const DevBufs &d, int cur, const double *T, double *Q, double *B,
+                       double *FT, cudaStream_t st, int64_t *launches)
+{
+    k_thermal_fields<S><<<blocks_for(p.N), kThreads, 0, st>>>(p, typed(d, cur), T, Q, B, FT);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t do_fields(const KParams &p, const DevBufs &d, int cur, double *nbar, double *C, double *A, double *u,
                       cudaStream_t st, int64_t *launches)
 {
@@ -391,7 +399,7 @@ cudaError_t do_flow_step(const BatchLaunch &L, const FlowLaunch &F, cudaStream_t
 
 static_assert(sizeof(KBufs<S, T>) <= kKBufsMaxBytes, "KBufs larger than its table slot");
 const Launchers kL = {do_prepare,  sizeof(KBufs<S, T>), kbufs_fill,    do_batch_step, do_init,   do_fields,
-                      do_moments,  do_population,       do_stats,      do_flow_ok,    do_flow_step};
+                      do_moments,  do_population,       do_stats,      do_flow_ok,    do_flow_step, do_thermal};
 
 }  // namespace
 

@@ -111,6 +111,11 @@ struct Launchers {
     // and its launch: F.nsteps time steps of every slot in one kernel
     bool (*flow_ok)(const BatchLaunch &);
     cudaError_t (*flow_step)(const BatchLaunch &, const FlowLaunch &F, cudaStream_t, int64_t *launches);
+    // energy-equation fields Q, B, F^T (FP64 device arrays: N, 3N, 3N) on the
+    // temperature T (N doubles) from the state in buffer `cur`, after its
+    // moments and smeared density were updated by batch_step parts 0 and 1
+    cudaError_t (*thermal)(const KParams &, const DevBufs &, int cur, const double *T, double *Q, double *B,
+                           double *FT, cudaStream_t, int64_t *launches);
 };
 
 const Launchers &launchers_f64();

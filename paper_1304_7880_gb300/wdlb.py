@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH):
         "wdlb_moments": (I32, [P, P, P]),
         "wdlb_moments_device": (I32, [P, P, P]),
         "wdlb_fields": (I32, [P, P, P, P, P]),
+        "wdlb_thermal_fields": (I32, [P, P, P, P, P]),
         "wdlb_get_populations": (I32, [P, P]),
         "wdlb_pore_average": (I32, [P, P]),
         "wdlb_run_steady": (I32, [P, D, I32, I64, P, P]),
@@ -264,6 +265,19 @@ def wdlb_fields(ctx: Context):
     u = np.empty((3,) + ctx.shape)
     _check(lib.wdlb_fields(ctx.handle, _ptr(nbar), _ptr(C), _ptr(A), _ptr(u)), ctx)
     return nbar, C, A, u
+
+
+def wdlb_thermal_fields(ctx: Context, T):
+    """Energy-equation fields of Sec. 3 on a prescribed temperature T (k_B T per
+    node, lattice units; shape (nz, ny, nx)): (Q, B, FT) with shapes
+    (nz, ny, nx), (3, nz, ny, nx), (3, nz, ny, nx) (Eq. campob1, Eq. campos,
+    Eq. thermalforce)."""
+    T = np.ascontiguousarray(T, dtype=np.float64).reshape(ctx.shape)
+    Qf = np.empty(ctx.shape)
+    B = np.empty((3,) + ctx.shape)
+    FT = np.empty((3,) + ctx.shape)
+    _check(load_library().wdlb_thermal_fields(ctx.handle, _ptr(T), _ptr(Qf), _ptr(B), _ptr(FT)), ctx)
+    return Qf, B, FT
 
 
 def wdlb_get_populations(ctx: Context) -> np.ndarray:
