@@ -32,6 +32,7 @@
 namespace wdlb {
 namespace tiled {
 
+
 constexpr int TX = 8, TY = 8;
 constexpr int kVariants = 3;
 
@@ -237,13 +238,13 @@ constexpr bool tma_staging()
 // blocks' shared memory fits (227 KB per SM; the compiler then keeps to 85
 // registers per thread), else two where two fit, else one; one for 512
 // threads.  Three blocks measured 7-12 % faster than two for sigma 3 (8^3
-// bricks) and sigma 4 (8 x 8 x 4 bricks).  The double-word collision (DW)
-// needs more than 85 registers: at most two blocks.
-template <int S2, int V, bool WT = false, bool DW = false>
+// bricks) and sigma 4 (8 x 8 x 4 bricks), and 5 % faster for the double-word
+// collision at sigma 4, whose 85 registers spill ~100 bytes.
+template <int S2, int V, bool WT = false>
 constexpr int blocks_per_sm()
 {
     return threads_of(V) != 256                                ? 1
-           : !DW && 3 * smem_bytes<S2, V, WT>() <= size_t(227) * 1024 ? 3
+           : 3 * smem_bytes<S2, V, WT>() <= size_t(227) * 1024 ? 3
            : 2 * smem_bytes<S2, V, WT>() <= size_t(227) * 1024 ? 2
                                                                 : 1;
 }

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) k_step_shell(const KParams *P, const KBuf
 }
 
 template <class S, int S2, int V, bool WALLS, bool WT, class A = float>
-__global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2, V, WT, is_dw<A>::value>()))
+__global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2, V, WT>()))
     k_step_shell_tiled(const KParams *P, const KBufs<S, float> *B, const BatchItem *it)
 {
     const BatchItem w = it[blockIdx.x];
@@ -121,7 +121,7 @@ __device__ __forceinline__ int ld_acquire_gpu(const int *p)
 }
 
 template <class S, int S2, int V, bool WALLS, bool WT, class A = float>
-__global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2, V, WT, is_dw<A>::value>()))
+__global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2, V, WT>()))
     k_step_flow(FlowArgs a)
 {
     typedef typename Store<S>::T T;
