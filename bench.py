@@ -150,6 +150,33 @@ def kernel_source_hash():
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_shell_tiled_batch64_traffic.txt")
+STEP_BYTES_FILE = os.path.join(ROOT, "profiles", "step_bulk128_dram_record.txt")
+
+
+def _record(path):
+    rec = {}
+    try:
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+    except OSError:
+        pass
+    return rec
+
+
+def recorded_step_bytes(rule):
+    """Measured DRAM bytes per node update of the whole FP32 128^3 step (moments,
+    smeared density and shell kernels) with the given shell rule, from the
+    committed ncu record, used only if taken on the current kernel sources."""
+    rec = _record(STEP_BYTES_FILE)
+    try:
+        if rec.get("source_hash") == kernel_source_hash():
+            return float(rec["bytes_per_node_" + rule])
+    except (KeyError, ValueError):
+        pass
+    return None
 
 
 def recorded_traffic(nodes):
@@ -690,6 +717,10 @@ def run_ours(args):
         out = {"value": mlups, "unit": UNIT, "kernels_ms": pk, "tile_shape": w.wdlb_tile_info(c2)[1],
                "hbm_frac_of_measured": mlups * 1e6 * BYTES_PER_NODE[storage] / 1e9 / peaks["hbm_gbs"]}
         if storage == "f32":
+            measured = recorded_step_bytes(rule)
+            out.update({"measured_bytes_per_node": measured,
+                        "hbm_frac_from_measured_bytes": None if measured is None else
+                        mlups * 1e6 * measured / 1e9 / peaks["hbm_gbs"]})
             ns = len(w.wdlb_shell_table(SIGMA, rule)[1]) if rule == "compact" else shell_size(SIGMA)
             fl = ns * (FLOPS_PER_PAIR_WEIGHTED if rule == "compact" else FLOPS_PER_PAIR) + FLOPS_COLLIDE
             tf = fl * N / (pk[2] * 1e-3) / 1e12

@@ -16,6 +16,8 @@
  * state and of the moments and smeared density.  Each fluid node then takes one
  * of three variants of the field and collision arithmetic:
  *   ff  pair weights, accumulators, forces and collision in float (the kernel);
+ *   fd  pair weights, accumulators and forces in float, collision in double
+ *       (the arithmetic the library's double-word collision carries out);
  *   df  pair weights, accumulators and forces in double, collision in float;
  *   dd  all of it in double.
  * Nodes within `band` layers of a wall take the variant `band_mode`, the rest
@@ -158,6 +160,14 @@ static void node_ff(int z, int nxt, double *new_nscale)
 {
 #include "column_node.h"
 }
+#undef TC
+#define TC double
+static void node_fd(int z, int nxt, double *new_nscale)
+{
+#include "column_node.h"
+}
+#undef TC
+#define TC float
 #undef TW
 #undef FETCH
 #define TW double
@@ -180,9 +190,10 @@ typedef void (*node_fn)(int, int, double *);
 static node_fn variant(const char *s)
 {
     if (!strcmp(s, "ff")) return node_ff;
+    if (!strcmp(s, "fd")) return node_fd;
     if (!strcmp(s, "df")) return node_df;
     if (!strcmp(s, "dd")) return node_dd;
-    fprintf(stderr, "mode must be ff, df or dd\n");
+    fprintf(stderr, "mode must be ff, fd, df or dd\n");
     exit(2);
 }
 

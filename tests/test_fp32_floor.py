@@ -18,6 +18,9 @@ notes rest on:
 * The kernel's form, [(G+ + G-)(dn+ - dn-) + (G+ - G-)(n+ + n-)]/2, is odd
   under swapping the ends bit for bit: the net x-force drops below 1e-5 of the
   drive, the u_x error to ~2e-5 and the flux error to ~4e-6.
+* With the pair loop in FP32 and only the collision wide (the arithmetic the
+  library's double-word collision carries out) u_x is within 1e-5 (4.2e-6):
+  the collision carries the rest of the FP32 error.
 * FP32 storage with FP64 arithmetic gives u_x within 1e-5 (5.0e-6), but the
   wall-normal velocity, zero at steady state, keeps a noise of ~1e-4 of
   max|u_x| (1.4e-8 absolute): next to a wall the populations carry a momentum
@@ -104,3 +107,12 @@ def test_fp32_storage_floor(reference):
     assert eux < 1e-5 and ef < 1e-5             # measured 5.0e-6, 5.3e-7
     assert euz > 5e-5                           # wall-normal noise of the storage: 1.0e-4
     assert abs(inner) < 1e-9 * drive
+
+
+def test_wide_collision_reaches_the_storage_floor(reference):
+    x_ff, _, _ = _run("float", "ff", "sym")
+    x_fd, _, _ = _run("float", "fd", "sym")
+    _, eux_ff, _, _ = _errors(x_ff, reference)
+    _, eux, _, ef = _errors(x_fd, reference)
+    assert eux < 1e-5 and eux < eux_ff / 3      # measured 4.2e-6 (FP32 collision 2.1e-5)
+    assert ef < 2e-6                            # measured 9.3e-7
