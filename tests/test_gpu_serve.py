@@ -114,3 +114,35 @@ def test_server_rejects_a_pore_larger_than_its_budget(w):
         time.sleep(0.01)
     w.wdlb_server_destroy(srv)
     assert out and out[0]["id"] == rid and out[0]["status"] == 2
+
+
+def test_server_double_word_collision_results_equal_alone(w):
+    """A server with the double-word collision (sigma 3, 4 and 6 requests in one
+    batch, each its own tile kernel): every result equal bit for bit to the
+    request solved alone with that collision."""
+    reqs = [REQUESTS[0], REQUESTS[1], REQUESTS[5]]
+    srv = w.wdlb_server_create(64 << 20, max_active=4, check_every=100, collision="dw")
+    ids = {}
+    for k, (lat, sigma, nstar, gx, seed) in enumerate(reqs):
+        p, n, u = synth.slit_poiseuille(*lat, nstar, sigma, 1.0, gx, seed)
+        ids[w.wdlb_server_submit(srv, lat, sigma, True, 1.0, p["g"], n, u, tol=TOL, max_steps=200000,
+                                 want_moments=True)] = k
+    results = {}
+    t0 = time.time()
+    while len(results) < len(ids) and time.time() - t0 < 300:
+        for r in w.wdlb_server_poll(srv):
+            results[ids[r["id"]]] = r
+        time.sleep(0.01)
+    w.wdlb_server_destroy(srv)
+    assert len(results) == len(reqs)
+    for k, (lat, sigma, nstar, gx, seed) in enumerate(reqs):
+        r = results[k]
+        assert r["status"] == 0 and r["residual"] < TOL
+        p, n, u = synth.slit_poiseuille(*lat, nstar, sigma, 1.0, gx, seed)
+        ctx = w.wdlb_create(lat, sigma, True, 1.0, p["g"], storage="f32", collision="dw")
+        w.wdlb_init_fields(ctx, n, u)
+        steps, _ = w.wdlb_run_steady(ctx, TOL, 100, 200000)
+        n_a, u_a = w.wdlb_moments(ctx)
+        w.wdlb_destroy(ctx)
+        assert r["steps"] == steps
+        assert np.array_equal(r["n"], n_a) and np.array_equal(r["u"], u_a)

@@ -92,3 +92,29 @@ def test_non_positive_temperature_is_refused(w):
     T[0] = -1.0                 # solid plane: ignored
     w.wdlb_thermal_fields(ctx, T)
     w.wdlb_destroy(ctx)
+
+
+def test_collisional_conductivity_on_the_gpu(w, oracle_mod):
+    """Q on a sinusoidal temperature in a uniform fluid at rest, through the
+    CUDA path (FP64 storage), extrapolated to long waves: the collisional
+    conductivity of Eq. thermalcond, (2/3) sqrt(pi T) g2 n^2 sigma^4, times the
+    shell's second-moment ratio sum_e w e_x^2 / (4 pi sigma^2 / 3)."""
+    sigma, nstar, T0, a = 4.0, 0.4, 0.35, 1e-4
+    n0 = nstar / sigma ** 3
+    chi = np.pi * sigma ** 3 / 6 * n0
+    g2 = (1 - 0.5 * chi) / (1 - chi) ** 3
+    e, wsh = oracle_mod.shell(sigma)
+    ratio = float(np.sum(wsh * e[:, 0] ** 2)) / (4 * np.pi * sigma ** 2 / 3)
+    vals = []
+    for L in (128, 256):
+        kappa = 2 * np.pi / L
+        ctx = w.wdlb_create((L, 8, 8), sigma, False, 1.0, (0.0, 0.0, 0.0), storage="f64")
+        w.wdlb_init_fields(ctx, np.full((8, 8, L), n0))
+        T = np.broadcast_to(T0 + a * np.sin(kappa * np.arange(L)), (8, 8, L))
+        Qf, _, _ = w.wdlb_thermal_fields(ctx, T)
+        w.wdlb_destroy(ctx)
+        vals.append(Qf[0, 0, L // 4] / (-a * kappa ** 2) / np.sqrt(T0 + a))
+    got = (4 * vals[1] - vals[0]) / 3
+    want = (2.0 / 3.0) * np.sqrt(np.pi) * g2 * n0 ** 2 * sigma ** 4 * ratio
+    print("lambda_c / sqrt(T): GPU %.10e, paper x shell ratio %.10e (ratio %.4f)" % (got, want, ratio))
+    assert abs(got / want - 1) < 2e-5
