@@ -60,7 +60,8 @@
  *   R8  walls: nodes z = 0 and z = nz-1 are solid (n = 0 there, also beyond
  *       them); half-way bounce-back; x and y (and z without walls) periodic.
  *   R9  omega: constant 1/tau, or tau(r) - 1/2 scaled by
- *       n_ref g(n_ref) / (nbar(r) g(nbar(r))) (SMDB omega0 proportional to n g).
+ *       n_ref g(n_ref) / (nbar(r) g(nbar(r))) (SMDB omega0 proportional to n g),
+ *       n_ref the mean fluid density of the initial state unless given.
  */
 #include <math.h>
 #include <stdint.h>
@@ -347,6 +348,7 @@ typedef struct {
     int nx, ny, nz, walls;
     long N;
     double sigma, tau, g[3], k_cross, n_ref;
+    double n_ref_opt;                  /* reference density asked for; 0: see wo_init */
     int closure, omega_mode, interactions;
     int nball, nshell;
     int *ball, *shell;
@@ -406,7 +408,7 @@ wo_state *wo_create(int nx, int ny, int nz, int walls, double sigma, double tau,
     s->N = (long)nx * ny * nz;
     s->sigma = sigma; s->tau = tau; s->g[0] = gx; s->g[1] = gy; s->g[2] = gz;
     s->closure = closure; s->omega_mode = omega_mode; s->k_cross = k_cross;
-    s->n_ref = n_ref; s->interactions = interactions;
+    s->n_ref = s->n_ref_opt = n_ref; s->interactions = interactions;
     s->nball = wo_ball(sigma, NULL, 0);
     s->ball = (int *)malloc(sizeof(int) * 3 * s->nball);
     wo_ball(sigma, s->ball, s->nball);
@@ -467,6 +469,21 @@ int wo_init(wo_state *s, const double *n0, const double *u0)
     for (long i = 0; i < N; i++) {
         int z = (int)(i / ((long)s->nx * s->ny));
         for (int d = 0; d < 3; d++) s->vprev[d * N + i] = is_wall(s, z) ? 0.0 : u0[d * N + i];
+    }
+    /* R9's reference density, unless given: the mean density over the fluid
+     * nodes of the initial state */
+    if (s->n_ref_opt > 0.0) {
+        s->n_ref = s->n_ref_opt;
+    } else {
+        double sum = 0.0;
+        long fluid = 0;
+        for (long i = 0; i < N; i++) {
+            int z = (int)(i / ((long)s->nx * s->ny));
+            if (is_wall(s, z)) continue;
+            sum += n0[i];
+            fluid++;
+        }
+        s->n_ref = sum / (double)fluid;
     }
     s->steps = 0;
     s->unstable = 0;

@@ -178,3 +178,26 @@ def test_dw_refused_outside_fp32_slits(w):
         w.wdlb_batch_add(b, (16, 16, 16), 4.0, False, 1.0, (0.0, 0.0, 0.0), n, u)
     assert ei.value.status == 1
     w.wdlb_batch_destroy(b)
+
+
+@pytest.mark.parametrize("closure,omega_mode,collision", [("PY", "const", "dw"), ("CS", "nbar", "dw"),
+                                                            ("CS", "nbar", "fp32")])
+def test_dw_other_closures_and_relaxation_modes(w, oracle_mod, closure, omega_mode, collision):
+    """The double-word collision on the generic shell kernel (Percus-Yevick
+    closure) and with the relaxation rate from the smeared density (the FP32
+    collision too), the reference density left to its default (the initial
+    fluid mean): a noisy slit, 20 steps, against the oracle within the FP32
+    slit bounds."""
+    lat, g = (12, 10, 23), (1e-5, 0.0, 0.0)
+    n, u = synth.uniform_with_noise(*lat, 0.4 / 64, 2e-2, 9, True)
+    ctx = w.wdlb_create(lat, 4.0, True, 0.9, g, storage="f32", collision=collision, closure=closure,
+                        omega_mode=omega_mode)
+    w.wdlb_init_fields(ctx, n, u)
+    o = oracle_mod.Oracle(*lat, True, 4.0, 0.9, g, closure=closure, omega_mode=omega_mode)
+    o.init(n, u)
+    w.wdlb_step(ctx, 20)
+    o.step(20)
+    en, ec = _errors(w, ctx, o)
+    print("%s %s %s 20 steps: n %.2e, u_x %.2e, u_y %.2e, u_z %.2e" % (collision, closure, omega_mode, en, *ec))
+    assert en < 1e-6 and max(ec) < 5e-4
+    w.wdlb_destroy(ctx)

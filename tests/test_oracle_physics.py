@@ -175,5 +175,27 @@ def test_nbar_relaxation_mode_viscosity(oracle_mod):
     chi = lambda n: math.pi * sigma ** 3 * n / 6
     tau_eff = 0.5 + (tau - 0.5) * (2 * n0 * g_cs(chi(2 * n0))) / (n0 * g_cs(chi(n0)))
     assert rate(tau=tau, omega_mode="nbar", n_ref=n0) == pytest.approx(rate(tau=tau), rel=1e-9)
+    # without n_ref the reference is the initial fluid mean, here n0
+    assert rate(tau=tau, omega_mode="nbar") == pytest.approx(rate(tau=tau), rel=1e-9)
     assert rate(tau=tau, omega_mode="nbar", n_ref=2 * n0) == pytest.approx(rate(tau=tau_eff), rel=1e-9)
     assert rate(tau=tau_eff) == pytest.approx(KT * (tau_eff - 0.5) * q * q, rel=0.03)
+
+
+def test_nbar_mode_default_reference_is_the_fluid_mean(oracle_mod):
+    """In a slit the default reference density of the nbar relaxation mode is
+    the initial mean over the fluid planes (the solid planes, whatever the
+    input holds there, do not count): the same run as with that mean given."""
+    nx, ny, nz = 6, 5, 17
+    rng = np.random.default_rng(4)
+    n = (0.4 / 64) * (1 + 0.02 * rng.standard_normal((nz, ny, nx)))
+    n[0], n[-1] = 0.03, 0.05                   # ignored: solid planes
+    mean = n[1:-1].mean()
+    runs = []
+    for kw in ({}, {"n_ref": mean}, {"n_ref": n.mean()}):
+        o = oracle_mod.Oracle(nx, ny, nz, True, 4.0, 0.9, (1e-5, 0.0, 0.0), omega_mode="nbar", **kw)
+        o.init(n)
+        o.step(5)
+        runs.append(o.moments()[1])
+    scale = np.abs(runs[0]).max()
+    assert np.abs(runs[0] - runs[1]).max() < 1e-12 * scale     # the two means differ in summation order
+    assert np.abs(runs[0] - runs[2]).max() > 1e-2 * scale      # the all-node mean: a different run
