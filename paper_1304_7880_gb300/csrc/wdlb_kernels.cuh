@@ -444,6 +444,35 @@ __device__ __forceinline__ void shell_forces(const KParams &p, const ShellAcc<T>
 // tsum = t of the field-velocity predictor for the next step.  FIELDS: write
 // nbar, C, A and the collision velocity instead of advancing the state.
 // ---------------------------------------------------------------------------
+// Index offsets from node (x, y, z) to its neighbours one step down and up
+// each axis, wrapped periodically in x and y (and z without walls; with walls,
+// z +- 1 of a fluid node lies in the lattice).  Formed once per node, so that
+// the push of every direction is the same branch-free sum of three offsets.
+struct PushOffsets {
+    int xm, xp, ym, yp, zm, zp;
+};
+
+template <bool WALLS>
+__device__ __forceinline__ PushOffsets push_offsets(int x, int y, int z, int nx, int ny, int nz)
+{
+    const int nxy = nx * ny;
+    PushOffsets o;
+    o.xm = x > 0 ? -1 : nx - 1;
+    o.xp = x < nx - 1 ? 1 : 1 - nx;
+    o.ym = y > 0 ? -nx : (ny - 1) * nx;
+    o.yp = y < ny - 1 ? nx : (1 - ny) * nx;
+    o.zm = WALLS || z > 0 ? -nxy : (nz - 1) * nxy;
+    o.zp = WALLS || z < nz - 1 ? nxy : (1 - nz) * nxy;
+    return o;
+}
+
+// i + c for a lattice direction c with components in {-1, 0, 1}
+__device__ __forceinline__ int push_target(const PushOffsets &o, int i, int cx, int cy, int cz)
+{
+    return i + (cx < 0 ? o.xm : cx > 0 ? o.xp : 0) + (cy < 0 ? o.ym : cy > 0 ? o.yp : 0) +
+           (cz < 0 ? o.zm : cz > 0 ? o.zp : 0);
+}
+
 // target_dn(q, dst) returns n - n_off of the node a population is pushed to
 // (this step's density there: its storage scale for the next step).
 template <class S, int CL, bool WALLS, bool FIELDS, class T, class TargetDn>
@@ -501,10 +530,7 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
     const T uu = ux * ux + uy * uy + uz * uz;
     const T uF = ux * Fx + uy * Fy + uz * Fz;
     const T src_pref = T(1) - T(0.5) * omega;
-    // a node off the periodic edges of the lattice pushes to i + c_q without
-    // wrapping (with walls, z +- 1 of a fluid node is a fluid node or a wall)
-    const int nxy = nx * ny;
-    const bool inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && (WALLS || (z > 0 && z < nz - 1));
+    const PushOffsets po = push_offsets<WALLS>(x, y, z, nx, ny, nz);
 
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
@@ -520,7 +546,7 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
         const T post = d[q] - omega * (d[q] - feq_dev) + src_pref * (phi + sa);
         // push streaming with half-way bounce-back; re-encode relative to the
         // target's rest state w_q s(target), s(target) = its density now
-        int zt = z + czq;
+        const int zt = z + czq;
         int dst;
         int qq = q;
         T dn_t;
@@ -529,14 +555,7 @@ __device__ __forceinline__ void collide_push(const KParams &p, const KBufs<S, T>
             qq = opp_of(q);
             dn_t = dn_self;
         } else {
-            if (inner) {
-                dst = i + cxq + cyq * nx + czq * nxy;
-            } else {
-                if (!WALLS) zt = wrap_coord(zt, nz);
-                const int xt = wrap_coord(x + cxq, nx);
-                const int yt = wrap_coord(y + cyq, ny);
-                dst = xt + nx * (yt + ny * zt);
-            }
+            dst = push_target(po, i, cxq, cyq, czq);
             dn_t = q == 0 ? dn_self : target_dn(q, dst);
         }
         if (!in_bounds(dst, p.N, b.status)) continue;
@@ -624,8 +643,7 @@ __device__ __forceinline__ void collide_push_dw(const KParams &p, const KBufs<S,
     const dwf uu15 = (ux * ux + uy * uy + uz * uz) * 1.5f;
     const dwf uF = ux * Fx + uy * Fy + uz * Fz;
     const dwf src_pref = dw_from(1.f) - dw_scale2(omega, 0.5f);
-    const int nxy = nx * ny;
-    const bool inner = x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && (WALLS || (z > 0 && z < nz - 1));
+    const PushOffsets po = push_offsets<WALLS>(x, y, z, nx, ny, nz);
 
 #pragma unroll
     for (int q = 0; q < NQ; q++) {
@@ -644,7 +662,7 @@ __device__ __forceinline__ void collide_push_dw(const KParams &p, const KBufs<S,
         if (cyq && czq) cAc = cAc + float(2 * cyq * czq) * Ayz;
         const dwf sa = kA * wq * cAc;
         const dwf post = d[q] - omega * (d[q] - feq_dev) + src_pref * (phi + sa);
-        int zt = z + czq;
+        const int zt = z + czq;
         int dst;
         int qq = q;
         float dn_t;
@@ -653,14 +671,7 @@ __device__ __forceinline__ void collide_push_dw(const KParams &p, const KBufs<S,
             qq = opp_of(q);
             dn_t = dn_self;
         } else {
-            if (inner) {
-                dst = i + cxq + cyq * nx + czq * nxy;
-            } else {
-                if (!WALLS) zt = wrap_coord(zt, nz);
-                const int xt = wrap_coord(x + cxq, nx);
-                const int yt = wrap_coord(y + cyq, ny);
-                dst = xt + nx * (yt + ny * zt);
-            }
+            dst = push_target(po, i, cxq, cyq, czq);
             dn_t = q == 0 ? dn_self : target_dn(q, dst);
         }
         if (!in_bounds(dst, p.N, b.status)) continue;
