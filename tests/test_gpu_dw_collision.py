@@ -22,6 +22,8 @@ import pytest
 
 from paper_1304_7880_gb300 import synth
 
+from oracle_views import collision_velocity
+
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "slit_column_steady.txt")
@@ -84,8 +86,14 @@ def test_dw_slit_8x8x41(w, oracle_mod):
     n_o, u_o = o.moments()
     ref = oracle_mod.pore_average(n_o, u_o, True, p["g"][0])
     ef = abs(st["flux_x"] - ref["flux_x"]) / abs(ref["flux_x"])
-    print("dw 8x8x41 1000 steps: n %.2e, u_x %.2e, u_y %.2e, u_z %.2e, flux %.2e" % (en, *ec, ef))
+    uc_g = w.wdlb_fields(ctx)[3]
+    uc_o = collision_velocity(oracle_mod, o, p["g"])
+    fl = slice(1, -1)
+    ecc = [np.abs(uc_g[a, fl] - uc_o[a, fl]).max() / np.abs(uc_o[0, fl]).max() for a in range(3)]
+    print("dw 8x8x41 1000 steps: n %.2e, u_x %.2e, u_y %.2e, u_z %.2e, flux %.2e; collision u_x %.2e, u_y %.2e, "
+          "u_z %.2e" % (en, *ec, ef, *ecc))
     assert en < 1e-6 and ef < 1e-5 and max(ec) < 5e-4    # measured flux 3.1e-6, u_x 1.0e-4, u_z 4.2e-4
+    assert max(ecc) < 5e-4                               # measured u_x 1.0e-4, u_z 2.5e-4
     w.wdlb_destroy(ctx)
 
 
@@ -120,14 +128,17 @@ def test_dw_steady_slit_256x256x161(w, n_star):
     steps = 3 * ref["steps"]
     w.wdlb_step(ctx, steps)
     n_g, u_g = w.wdlb_moments(ctx)
+    uc_g = w.wdlb_fields(ctx)[3]
     w.wdlb_destroy(ctx)
     n_z, u_z = n_g[1:-1, 0, 0], u_g[0, 1:-1, 0, 0]
     n_o, u_o = ref["n"][1:-1], ref["ux"][1:-1]
     en = np.max(np.abs(n_z - n_o) / n_o)
     eu = np.max(np.abs(u_z - u_o)) / np.abs(u_o).max()
     eq = abs(np.sum(n_z * u_z) / np.sum(n_o * u_o) - 1)
-    print("dw n* %g: %d steps, n %.2e, u_x %.2e, flux %.2e" % (n_star, steps, en, eu, eq))
-    assert en < 1e-6 and eu < 1e-5 and eq < 1e-5
+    # converged: the collision velocity u equals the oracle's v (reading R7)
+    euc = np.max(np.abs(uc_g[0, 1:-1, 0, 0] - u_o)) / np.abs(u_o).max()
+    print("dw n* %g: %d steps, n %.2e, u_x %.2e, flux %.2e, collision u_x %.2e" % (n_star, steps, en, eu, eq, euc))
+    assert en < 1e-6 and eu < 1e-5 and eq < 1e-5 and euc < 1e-5
 
 
 PORES = [((16, 16, 25), 1e-5, 0.4, 41), ((32, 24, 61), 3e-6, 0.5, 42), ((8, 8, 41), 1e-6, 0.3, 43),

@@ -79,6 +79,7 @@ def test_steady_slit_against_oracle(w, storage, n_star):
     steps = STEP_FACTOR * ref["steps"]
     w.wdlb_step(ctx, steps)
     n_g, u_g = w.wdlb_moments(ctx)
+    uc_g = w.wdlb_fields(ctx)[3]
     w.wdlb_destroy(ctx)
     # uniform in x and y
     assert np.array_equal(n_g, np.broadcast_to(n_g[:, :1, :1], n_g.shape))
@@ -88,10 +89,12 @@ def test_steady_slit_against_oracle(w, storage, n_star):
     eu = np.max(np.abs(u_z - u_o)) / np.abs(u_o).max()
     q_g, q_o = np.sum(n_z * u_z), np.sum(n_o * u_o)
     eq = abs(q_g - q_o) / abs(q_o)
+    # converged: the collision velocity u equals the oracle's v (reading R7)
+    euc = np.max(np.abs(uc_g[0, 1:-1, 0, 0] - u_o)) / np.abs(u_o).max()
     bn, bu, bq = BOUNDS[storage]
-    print("n* %g %s: %d steps (oracle %d), n %.2e, u_x %.2e, flux %.2e"
-          % (n_star, storage, steps, ref["steps"], en, eu, eq))
-    assert en < bn and eu < bu and eq < bq, (en, eu, eq)
+    print("n* %g %s: %d steps (oracle %d), n %.2e, u_x %.2e, flux %.2e, collision u_x %.2e"
+          % (n_star, storage, steps, ref["steps"], en, eu, eq, euc))
+    assert en < bn and eu < bu and eq < bq and euc < bu, (en, eu, eq, euc)
 
 
 def test_full_size_slit_stays_uniform_in_xy(w):
