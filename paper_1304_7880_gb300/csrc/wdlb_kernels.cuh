@@ -312,9 +312,9 @@ __device__ __forceinline__ void ball_brick_ct(const KParams &p, const V4<T> *nu,
 // Carnahan-Starling value one multiply-add: 2 g2 = (1 + s)/s^3 with
 // s = 1 - chi_mid (Percus-Yevick: (3 - s)/s^2; closure one: 2).  s0 = 1 - h(r)
 // - h_off; dh, dn: deviations of the two neighbours.  Besides Q+ and Q- it
-// returns Q+ - Q-, formed from the deviations so that it is accurate relative
-// to itself (it is what the mean-field sum accumulates):
-//   Q+ - Q- = [(G+ + G-)(dn+ - dn-) + (G+ - G-)(n+ + n-)] / 2,   G = 2 g2,
+// returns 2 (Q+ - Q-), formed from the deviations so that it is accurate
+// relative to itself (it is what the mean-field sum accumulates):
+//   2 (Q+ - Q-) = (G+ + G-)(dn+ - dn-) + (G+ - G-)(n+ + n-),   G = 2 g2,
 //   CS:  G+ - G- = (dh+ - dh-) [s+^2 + s-^2 + s+ s- (1 + s+ + s-)] / (s+^3 s-^3)
 //   PY:  G+ - G- = (dh+ - dh-) [3 (s+ + s-) - s+ s-] / (s+^2 s-^2)
 // (exact divided differences of the closures; s- - s+ = dh+ - dh-).
@@ -346,7 +346,7 @@ __device__ __forceinline__ void pair_weights(T s0, T noff, T dhp, T dnp, T dhm, 
     if (CL == 2) {
         qp = T(2) * np;
         qm = T(2) * nm;
-        qd = T(2) * (dnp - dnm);
+        qd = T(4) * (dnp - dnm);
         return;
     }
     const T sp = s0 - dhp, sm = s0 - dhm;
@@ -371,13 +371,15 @@ __device__ __forceinline__ void pair_weights(T s0, T noff, T dhp, T dnp, T dhm, 
     // cancels between mirror pairs exactly where the state is mirror-symmetric.
     // (G+ (dn+ - dn-) + (G+ - G-) n- is the same number rounded differently at
     // each end; in a driven slit that left a net x-force of 0.3 % of the drive.)
-    qd = T(0.5) * fma(add_rn(gp, gm), dnp - dnm, gd * add_rn(np, nm));
+    // Returned doubled, 2 (Q+ - Q-): the halving is one exact scaling of the
+    // sum V in shell_forces instead of a product per pair.
+    qd = fma(add_rn(gp, gm), dnp - dnm, gd * add_rn(np, nm));
 }
 
 // Shell-sum accumulators (doubled weights Q = 2q, no quadrature weight w).
 // The velocity sums take the neighbours' velocities v' = v(r+e) directly; the
 // node's own velocity v enters W per pair and S once, in shell_forces:
-//   V    = sum Q khat                                      (F^mf)
+//   V    = 2 sum Q khat, doubled once more (halved in shell_forces)  (F^mf)
 //   W    = sum Q khat (khat . (v' - v))                    (F^viscous)
 //   S_ab = sum Q (khat_b v'_a + khat_a v'_b), diagonal once (A, before the
 //          term - (V_a v_b + V_b v_a) that turns v' into v' - v)
@@ -421,20 +423,22 @@ __device__ __forceinline__ void shell_forces(const KParams &p, const ShellAcc<T>
                                              T &Cy, T &Cz, T &Axx, T &Ayy, T &Azz, T &Axy, T &Axz, T &Ayz, T &tsum)
 {
     const T wh = T(0.5) * prm<T>(p.wshell, p.f_wshell);
+    // the mean-field sum, carried doubled (pair_weights): halving is exact
+    const T Vx = T(0.5) * a.Vx, Vy = T(0.5) * a.Vy, Vz = T(0.5) * a.Vz;
     const T mf = -T(CS2) * prm<T>(p.sig2, p.f_sig2) * wh * n;
     const T vi = prm<T>(p.beta, p.f_beta) * wh * n;
     // multiply-adds written out (the same bits in every kernel); the product
     // with the mean-field sum V, the larger term next to a wall, enters exactly
-    Cx = fma(mf, a.Vx, vi * a.Wx);
-    Cy = fma(mf, a.Vy, vi * a.Wy);
-    Cz = fma(mf, a.Vz, vi * a.Wz);
+    Cx = fma(mf, Vx, vi * a.Wx);
+    Cy = fma(mf, Vy, vi * a.Wy);
+    Cz = fma(mf, Vz, vi * a.Wz);
     const T pa = -(T(CS2) / T(5)) * prm<T>(p.sig2, p.f_sig2) * n * wh;
-    Axx = T(2) * pa * fma(-a.Vx, vx, a.Sxx);
-    Ayy = T(2) * pa * fma(-a.Vy, vy, a.Syy);
-    Azz = T(2) * pa * fma(-a.Vz, vz, a.Szz);
-    Axy = pa * (a.Sxy - fma(a.Vy, vx, a.Vx * vy));
-    Axz = pa * (a.Sxz - fma(a.Vz, vx, a.Vx * vz));
-    Ayz = pa * (a.Syz - fma(a.Vz, vy, a.Vy * vz));
+    Axx = T(2) * pa * fma(-Vx, vx, a.Sxx);
+    Ayy = T(2) * pa * fma(-Vy, vy, a.Syy);
+    Azz = T(2) * pa * fma(-Vz, vz, a.Szz);
+    Axy = pa * (a.Sxy - fma(Vy, vx, Vx * vy));
+    Axz = pa * (a.Sxz - fma(Vz, vx, Vx * vz));
+    Ayz = pa * (a.Syz - fma(Vz, vy, Vy * vz));
     tsum = a.t * wh;
 }
 
