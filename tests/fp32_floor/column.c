@@ -14,8 +14,11 @@
  *
  * Precision: STORE (compile time, float or double) is the type of the stored
  * state and of the moments and smeared density.  Each fluid node then takes one
- * of three variants of the field and collision arithmetic:
- *   ff  pair weights, accumulators, forces and collision in float (the kernel);
+ * of these variants of the field and collision arithmetic:
+ *   fc  pair weights, accumulators, forces and collision in float, with the
+ *       in-plane momentum correction of the collision (the kernel in slits);
+ *   ff  the same without the correction (the kernel's collision in periodic
+ *       boxes);
  *   fd  pair weights, accumulators and forces in float, collision in double
  *       (the arithmetic the library's double-word collision carries out);
  *   df  pair weights, accumulators and forces in double, collision in float;
@@ -153,6 +156,7 @@ static void ball(void)
 DEFINE_FETCH(fetch_f, float)
 DEFINE_FETCH(fetch_d, double)
 
+#define CORR 0
 #define TW float
 #define TC float
 #define FETCH fetch_f
@@ -160,6 +164,14 @@ static void node_ff(int z, int nxt, double *new_nscale)
 {
 #include "column_node.h"
 }
+#undef CORR
+#define CORR 1
+static void node_fc(int z, int nxt, double *new_nscale)
+{
+#include "column_node.h"
+}
+#undef CORR
+#define CORR 0
 #undef TC
 #define TC double
 static void node_fd(int z, int nxt, double *new_nscale)
@@ -185,15 +197,17 @@ static void node_dd(int z, int nxt, double *new_nscale)
 #undef TW
 #undef TC
 #undef FETCH
+#undef CORR
 
 typedef void (*node_fn)(int, int, double *);
 static node_fn variant(const char *s)
 {
     if (!strcmp(s, "ff")) return node_ff;
+    if (!strcmp(s, "fc")) return node_fc;
     if (!strcmp(s, "fd")) return node_fd;
     if (!strcmp(s, "df")) return node_df;
     if (!strcmp(s, "dd")) return node_dd;
-    fprintf(stderr, "mode must be ff, fd, df or dd\n");
+    fprintf(stderr, "mode must be fc, ff, fd, df or dd\n");
     exit(2);
 }
 

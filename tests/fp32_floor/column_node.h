@@ -5,7 +5,9 @@
  * precision variant: TW is the type of the pair weights, accumulators and
  * forces, TC the type of the collision, FETCH the neighbour loader of type TW.
  * Q+ - Q- takes the kernel's form, odd under swapping the pair's ends bit for
- * bit, or (QD_ASYM) the earlier G+ (dn+ - dn-) + (G+ - G-) n-. */
+ * bit, or (QD_ASYM) the earlier G+ (dn+ - dn-) + (G+ - G-) n-.  CORR adds the
+ * kernel's in-plane momentum correction of the FP32 collision in slits (the
+ * double sum here stands for its double-word sum). */
         TW noff=(TW)NOFF, hoff=(TW)HOFF, hr = hoff + (TW)hb[z], s0 = (TW)1 - hr - hoff;
         TW me_dn=(TW)nudn[z], vx=(TW)nuv[0][z], vy=(TW)nuv[1][z], vz=(TW)nuv[2][z];
         TW Vx=0,Vy=0,Vz=0,Wx=0,Wy=0,Wz=0,Sxx=0,Syy=0,Szz=0,Sxy=0,Sxz=0,Syz=0,t=0;
@@ -46,11 +48,31 @@
         TC Bxx=(TC)Axx-tr3,Byy=(TC)Ayy-tr3,Bzz=(TC)Azz-tr3, kA=(TC)2*(TC)4.5;
         TC uu=u[0]*u[0]+u[1]*u[1]+u[2]*u[2], uF=u[0]*F[0]+u[1]*F[1]+u[2]*F[2], src=(TC)1-(TC)0.5*om;
         TC dn_self=(TC)me_dn;
+        /* post-collision values; with CORR in the corrected kernel's form,
+         * post = d + change, and the changes' in-plane momentum summed */
+        TC post_all[Q]; double Mx=0, My=0;
         for(int q=0;q<Q;q++){
             TC wq=(TC)W[q], cu=(TC)C[q][0]*u[0]+(TC)C[q][1]*u[1]+(TC)C[q][2]*u[2], cF=(TC)C[q][0]*F[0]+(TC)C[q][1]*F[1]+(TC)C[q][2]*F[2];
             TC feq=wq*(dn+nn*((TC)3*cu+(TC)4.5*cu*cu-(TC)1.5*uu)), phi=wq*((TC)3*(cF-uF)+(TC)9*cu*cF);
             TC cAc=(TC)(C[q][0]*C[q][0])*Bxx+(TC)(C[q][1]*C[q][1])*Byy+(TC)(C[q][2]*C[q][2])*Bzz+(TC)(2*C[q][0]*C[q][1])*(TC)Axy+(TC)(2*C[q][0]*C[q][2])*(TC)Axz+(TC)(2*C[q][1]*C[q][2])*(TC)Ayz;
-            TC post=d[q]-om*(d[q]-feq)+src*(phi+kA*wq*cAc);
+            if (CORR) {
+                TC dl=src*(phi+kA*wq*cAc)-om*(d[q]-feq);
+                post_all[q]=d[q]+dl;
+                Mx+=(double)C[q][0]*(double)dl; My+=(double)C[q][1]*(double)dl;
+            } else {
+                post_all[q]=d[q]-om*(d[q]-feq)+src*(phi+kA*wq*cAc);
+            }
+        }
+        if (CORR) {
+            /* the kernel's in-plane momentum correction: the changes' x and y
+             * momentum (F exactly) summed without rounding error, and
+             * 3 w_q c_q . (F - sum) added back */
+            TC ex=(TC)3*(TC)((double)F[0]-Mx), ey=(TC)3*(TC)((double)F[1]-My);
+            for(int q=0;q<Q;q++) if(C[q][0]||C[q][1])
+                post_all[q]=(TC)fma((double)W[q], (double)((TC)C[q][0]*ex+(TC)C[q][1]*ey), (double)post_all[q]);
+        }
+        for(int q=0;q<Q;q++){
+            TC wq=(TC)W[q], post=post_all[q];
             int zt=z+C[q][2], dst=zt, qq=q; TC dnt;
             if(zt==0||zt==NZ-1){dst=z;qq=OPP[q];dnt=dn_self;} else dnt = (q==0)?dn_self:(TC)nudn[zt];
             f[nxt][qq][dst] = (STORE)(post + wq*(dsc-dnt));

@@ -21,6 +21,14 @@ notes rest on:
 * With the pair loop in FP32 and only the collision wide (the arithmetic the
   library's double-word collision carries out) u_x is within 1e-5 (4.2e-6):
   the collision carries the rest of the FP32 error.
+* The FP32 collision loses momentum to its own roundings: the changes
+  -omega (f - feq) + (1 - omega/2)(Phi + S^A) carry the momentum F exactly in
+  exact arithmetic, and their FP32 roundings bias a driven slit's steady flow
+  (the converged 161-node slit at n* 0.3: u_x 6.0e-5).  Summing the changes'
+  in-plane momentum without rounding error and adding 3 w_q c_q . (F - sum)
+  back (the kernel's collision with walls, variant fc) removes it: 6.1e-6
+  there; on an 81-node slit after 40 000 steps the flux error drops from
+  7.8e-6 to 3.9e-7.
 * FP32 storage with FP64 arithmetic gives u_x within 1e-5 (5.0e-6), but the
   wall-normal velocity, zero at steady state, keeps a noise of ~1e-4 of
   max|u_x| (1.4e-8 absolute): next to a wall the populations carry a momentum
@@ -116,3 +124,31 @@ def test_wide_collision_reaches_the_storage_floor(reference):
     _, eux, _, ef = _errors(x_fd, reference)
     assert eux < 1e-5 and eux < eux_ff / 3      # measured 4.2e-6 (FP32 collision 2.1e-5)
     assert ef < 2e-6                            # measured 9.3e-7
+
+
+def test_in_plane_momentum_correction(oracle_mod):
+    """The FP32 collision with the in-plane momentum correction (the kernel's
+    form in slits, variant fc) against the same collision without it (ff), on
+    an 81-node slit column (sigma 4, n* 0.3, tau 0.8, g_x 1e-6) after 40 000
+    steps from a uniform fluid at rest, both against the FP64 oracle."""
+    nz, steps = 81, 40000
+    args = [str(nz), "0.3", "4", "0.8", "1e-6", str(steps), "0"]
+    binary = _binary("float")
+    procs = {m: subprocess.Popen([binary] + args + [m, m, "sym"], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                 text=True) for m in ("ff", "fc")}
+    n = np.full((nz, 1, 1), 0.3 / 64)
+    n[0] = n[-1] = 0.0
+    o = oracle_mod.Oracle(1, 1, nz, True, 4.0, 0.8, (1e-6, 0.0, 0.0))
+    o.init(n)
+    o.step(steps)
+    nn, uu = o.moments()
+    ref = (nn[:, 0, 0], uu[0, :, 0, 0], uu[2, :, 0, 0])
+    err = {}
+    for m, pr in procs.items():
+        out, _ = pr.communicate()
+        assert pr.returncode == 0
+        err[m] = _errors(np.loadtxt(out.splitlines()), ref)
+    _, eux_ff, _, ef_ff = err["ff"]
+    _, eux_fc, _, ef_fc = err["fc"]
+    assert ef_ff > 4e-6 and eux_ff > 5e-6      # measured flux 7.8e-6, u_x 9.6e-6
+    assert ef_fc < 2e-6 and eux_fc < 5e-6      # measured flux 3.9e-7, u_x 1.9e-6
