@@ -642,7 +642,8 @@ def run_ours(args):
                                              "launch per phase)" % SUB)
     dw_leg = batch_leg(False, "dw", "double-word collision (WDLB_COLLISION_DW): the collision and the push's "
                                     "re-encoding in pairs of floats, FP32 storage; steady slit flows within 1e-5 of "
-                                    "the FP64 oracle on u_x and flux (FP32 collision: up to 5.4e-5)")
+                                    "the FP64 oracle on u_x and flux, as with the FP32 collision and its in-plane "
+                                    "momentum correction")
 
     # ---------------- end to end through the public batch API and host buffers ----------------
     pin = []

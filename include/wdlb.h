@@ -148,18 +148,21 @@ typedef struct {
                                  bitwise the same results                            */
     int32_t collision;        /* arithmetic of the collision and push (step 3 of
                                  Sec. 5, Eq. SMDB) with FP32 storage:
-                                 WDLB_COLLISION_FP32 (default) FP32;
-                                 WDLB_COLLISION_DW double-word pairs of floats
-                                 (~48-bit significands on the FP32 units), the
-                                 result rounded to FP32 once, at the store.  In a
-                                 driven slit each step changes the momentum by a
-                                 fraction ~ nu/H^2 of itself, and FP32 rounding of
-                                 the collision biases the steady flow (u_x and
-                                 flux errors up to ~6e-5 of max|u_x| at H = 159);
-                                 the double-word collision brings them to the
-                                 level FP32 storage sets (~6e-6).  Lattices with
-                                 walls and FP32 storage only (WDLB_ERR_ARG
-                                 otherwise; periodic boxes meet 1e-5 in FP32)   */
+                                 WDLB_COLLISION_FP32 (default) FP32; with walls
+                                 the momentum of its changes along the walls is
+                                 summed in double-word arithmetic and restored
+                                 (FP32 roundings otherwise lose momentum, and in
+                                 a driven slit, where each step changes it by a
+                                 fraction ~ nu/H^2 of itself, bias the steady
+                                 flow by up to ~6e-5 of max|u_x| at H = 159;
+                                 restored, ~5e-6);
+                                 WDLB_COLLISION_DW the whole collision in
+                                 double-word pairs of floats (~48-bit
+                                 significands on the FP32 units), the result
+                                 rounded to FP32 once, at the store (~5e-6 too).
+                                 Lattices with walls and FP32 storage only
+                                 (WDLB_ERR_ARG otherwise; periodic boxes meet
+                                 1e-5 in FP32)                                   */
 } wdlb_options;
 enum { WDLB_STAGING_AUTO = 0, WDLB_STAGING_CP_ASYNC = 1 };
 enum { WDLB_COLLISION_FP32 = 0, WDLB_COLLISION_DW = 1 };

@@ -4,7 +4,8 @@ floats, rounded to FP32 once at the store.
 
 * Against the FP64 oracle: the converged 256 x 256 x 161 slit (8 x 8
   cross-section, three times the oracle's steps) at n* 0.3 and 0.6 within
-  1e-5 on n, u_x and the pore flux (the FP32 collision: up to 5.4e-5); a
+  1e-5 on n, u_x and the pore flux (the FP32 collision without its in-plane
+  momentum correction: up to 5.4e-5); a
   short run of a noisy slit and the plain slit of Sec. 5's experiment at
   8 x 8 x 41 after 1000 steps within the FP32 slit bounds (there the 3-D
   flows the noise drives carry the FP32 fields' rounding, as with the FP32
