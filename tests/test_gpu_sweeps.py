@@ -67,6 +67,7 @@ def test_sweep_point_matches_oracle(sweeps, oracle_mod, chi, H):
     w.wdlb_step(ctx, 2 * steps)
     st = w.wdlb_pore_average(ctx)
     w.wdlb_destroy(ctx)
+    print("chi %.2f H %d: eta_eff rel err %.2e" % (chi, H, st["eta_eff"] / ref["eta_eff"] - 1))
     assert st["eta_eff"] == pytest.approx(ref["eta_eff"], rel=5e-4)
     assert st["mean_n"] == pytest.approx(ref["mean_n"], rel=1e-6)
     assert st["eta_eff"] / sweeps.bulk_shear_viscosity(st["mean_n"], SIGMA, TAU) < 1.0
