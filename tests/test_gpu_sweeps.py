@@ -41,9 +41,10 @@ def test_sweep_point_matches_oracle(sweeps, oracle_mod, chi, H):
     """A sweep width converged on both sides (the flux criterion can pass
     before a dense slit's density layering has relaxed, so the GPU lattice
     runs twice the oracle's step count): effective viscosity within the FP32
-    slit bound, 5e-4.  Measured 1.7e-4 (chi 0.11, H 16) and 1.0e-4 (chi 0.32,
-    H 24): in such thin slits the wall layers, where FP32 storage rounds the
-    x-momentum against the wall force, are a large part of the pore."""
+    slit bound, 5e-4.  Measured 2.3e-5 (chi 0.11, H 16) and 6.1e-5 (chi 0.32,
+    H 24); 1.7e-4 and 1.0e-4 before the FP32 collision restored its in-plane
+    momentum (in such thin slits the wall layers are a large part of the
+    pore)."""
     from paper_1304_7880_gb300 import synth
     from paper_1304_7880_gb300 import wdlb as w
     nz = H + 2
