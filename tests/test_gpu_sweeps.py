@@ -41,7 +41,7 @@ def test_sweep_point_matches_oracle(sweeps, oracle_mod, chi, H):
     """A sweep width converged on both sides (the flux criterion can pass
     before a dense slit's density layering has relaxed, so the GPU lattice
     runs twice the oracle's step count): effective viscosity within the FP32
-    slit bound, 5e-4.  Measured 2.3e-5 (chi 0.11, H 16) and 6.1e-5 (chi 0.32,
+    slit bound, 2e-4.  Measured 2.3e-5 (chi 0.11, H 16) and 6.1e-5 (chi 0.32,
     H 24); 1.7e-4 and 1.0e-4 before the FP32 collision restored its in-plane
     momentum (in such thin slits the wall layers are a large part of the
     pore)."""
@@ -69,7 +69,7 @@ def test_sweep_point_matches_oracle(sweeps, oracle_mod, chi, H):
     st = w.wdlb_pore_average(ctx)
     w.wdlb_destroy(ctx)
     print("chi %.2f H %d: eta_eff rel err %.2e" % (chi, H, st["eta_eff"] / ref["eta_eff"] - 1))
-    assert st["eta_eff"] == pytest.approx(ref["eta_eff"], rel=5e-4)
+    assert st["eta_eff"] == pytest.approx(ref["eta_eff"], rel=2e-4)
     assert st["mean_n"] == pytest.approx(ref["mean_n"], rel=1e-6)
     assert st["eta_eff"] / sweeps.bulk_shear_viscosity(st["mean_n"], SIGMA, TAU) < 1.0
 
