@@ -1189,6 +1189,11 @@ struct wdlb_batch {
     char *d_bufs[2] = {nullptr, nullptr};
     BatchItem *d_items = nullptr;
     size_t items_cap = 0;
+    // residual test in one set of launches: per-slot statistics buffers and
+    // the results [6P] and status words [P] of all slots
+    StatSlot *d_stat = nullptr;
+    double *d_res = nullptr;
+    int *d_st = nullptr;
     BatchLaunch launch{};
     bool dirty = true;
     int64_t steps_since_build = 0;
@@ -1260,6 +1265,7 @@ wdlb_status batch_build(wdlb_batch *b)
     TraceRange tr("batch_build");
     const int P = (int)b->slots.size();
     std::vector<KParams> params(P);
+    std::vector<StatSlot> stat(P, StatSlot{nullptr, nullptr, nullptr, nullptr});
     std::vector<char> bufs0(b->L->kbufs_bytes * P, 0), bufs1(b->L->kbufs_bytes * P, 0);
     std::vector<BatchItem> node_items, ball_items, ball_node_items;
     size_t ball_smem = 0;
@@ -1276,6 +1282,7 @@ wdlb_status batch_build(wdlb_batch *b)
         wdlb_ctx *c = b->slots[s].ctx;
         if (!c) continue;
         params[s] = c->kp;
+        stat[s] = StatSlot{c->dev.stage, c->dev.snap, c->dev.partial, c->dev.status};
         b->L->kbufs_fill(c->dev, c->cur, bufs0.data() + s * b->L->kbufs_bytes);
         b->L->kbufs_fill(c->dev, c->cur ^ 1, bufs1.data() + s * b->L->kbufs_bytes);
         const int N = (int)c->N;
@@ -1355,6 +1362,8 @@ wdlb_status batch_build(wdlb_batch *b)
         e = cudaMemcpyAsync(b->d_flow, counts.data(), 3 * P * sizeof(int), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && P > 0)
         e = cudaMemcpyAsync(b->d_params, params.data(), P * sizeof(KParams), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && P > 0)
+        e = cudaMemcpyAsync(b->d_stat, stat.data(), P * sizeof(StatSlot), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && P > 0)
         e = cudaMemcpyAsync(b->d_bufs[0], bufs0.data(), bufs0.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && P > 0)
@@ -1488,6 +1497,9 @@ wdlb_status wdlb_batch_create(const wdlb_options *opt, uint64_t pool_bytes, int3
     b->free_list.push_back(std::make_pair(size_t(0), b->pool_bytes));
     if (cudaMalloc(&b->d_flow, (6 * size_t(max_pores) + 8) * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&b->d_params, max_pores * sizeof(KParams)) != cudaSuccess ||
+        cudaMalloc(&b->d_stat, max_pores * sizeof(StatSlot)) != cudaSuccess ||
+        cudaMalloc(&b->d_res, 6 * size_t(max_pores) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->d_st, max_pores * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&b->d_bufs[0], max_pores * b->L->kbufs_bytes) != cudaSuccess ||
         cudaMalloc(&b->d_bufs[1], max_pores * b->L->kbufs_bytes) != cudaSuccess) {
         wdlb_batch_destroy(b);
@@ -1662,15 +1674,27 @@ wdlb_status wdlb_batch_residuals(wdlb_batch *b, int32_t interval, double *res, i
     const int P = (int)b->slots.size();
     std::vector<double> r(6 * P, 0.0);
     std::vector<int> stw(P, 0);
-    for (int s = 0; s < P; s++) {
-        wdlb_ctx *c = b->slots[s].ctx;
-        if (!c) continue;
-        cudaError_t e = c->L->stats(c->kp, c->dev, c->cur, 1, b->stream, &b->launches);
+    if (!b->dirty && P > 0) {
+        // every slot in three launches and two copies, with the partition and
+        // reduction order of the per-slot statistics (the same bits)
+        cudaError_t e = b->L->batch_stats(b->launch, (int)(b->steps_since_build & 1), b->d_stat, P, 1, b->d_res,
+                                          b->d_st, b->stream, &b->launches);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&r[6 * s], c->dev.result, 6 * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+            e = cudaMemcpyAsync(r.data(), b->d_res, 6 * size_t(P) * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&stw[s], c->dev.status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+            e = cudaMemcpyAsync(stw.data(), b->d_st, size_t(P) * sizeof(int), cudaMemcpyDeviceToHost, b->stream);
         if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch residuals: %s", cudaGetErrorString(e));
+    } else {
+        for (int s = 0; s < P; s++) {
+            wdlb_ctx *c = b->slots[s].ctx;
+            if (!c) continue;
+            cudaError_t e = c->L->stats(c->kp, c->dev, c->cur, 1, b->stream, &b->launches);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&r[6 * s], c->dev.result, 6 * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&stw[s], c->dev.status, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+            if (e != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch residuals: %s", cudaGetErrorString(e));
+        }
     }
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, WDLB_ERR_CUDA, "batch residuals sync");
     for (int s = 0; s < P; s++) {
@@ -1725,6 +1749,9 @@ void wdlb_batch_destroy(wdlb_batch *b)
         if (s.ctx) wdlb_destroy(s.ctx);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_params) cudaFree(b->d_params);
+    if (b->d_stat) cudaFree(b->d_stat);
+    if (b->d_res) cudaFree(b->d_res);
+    if (b->d_st) cudaFree(b->d_st);
     if (b->d_flow) cudaFree(b->d_flow);
     for (auto &p : b->d_bufs)
         if (p) cudaFree(p);

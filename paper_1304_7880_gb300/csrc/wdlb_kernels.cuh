@@ -912,12 +912,12 @@ __global__ void __launch_bounds__(256) k_pop_to_f64(KParams p, const S *f, const
 // Per-block FP64 partial sums over fluid nodes of the FP64 moments n, u_x:
 // [0] sum n, [1] sum u_x, [2] sum n u_x, [3] max |u_x - snap|, [4] max |u_x|, [5] count.
 // If update_snap, the snapshot is overwritten with the current u_x.
-static __global__ void __launch_bounds__(256) k_stats(KParams p, const double *n_, const double *ux_, double *snap,
-                                                      int update_snap, double *partial)
+__device__ __forceinline__ void stats_body(const KParams &p, const double *n_, const double *ux_, double *snap,
+                                           int update_snap, double *partial, int blk, int nblk)
 {
     __shared__ double sh[6][8];
     double a0 = 0, a1 = 0, a2 = 0, m3 = 0, m4 = 0, c5 = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p.N; i += gridDim.x * blockDim.x) {
+    for (int i = blk * blockDim.x + threadIdx.x; i < p.N; i += nblk * blockDim.x) {
         int z = i / (p.nx * p.ny);
         if (p.walls && (z == 0 || z == p.nz - 1)) continue;
         double n = n_[i], ux = ux_[i];
@@ -951,14 +951,20 @@ static __global__ void __launch_bounds__(256) k_stats(KParams p, const double *n
             r[0] += sh[0][w]; r[1] += sh[1][w]; r[2] += sh[2][w];
             r[3] = fmax(r[3], sh[3][w]); r[4] = fmax(r[4], sh[4][w]); r[5] += sh[5][w];
         }
-        for (int k = 0; k < 6; k++) partial[blockIdx.x * 6 + k] = r[k];
+        for (int k = 0; k < 6; k++) partial[blk * 6 + k] = r[k];
     }
 }
 
-static __global__ void k_stats_final(const double *partial, int nblocks, double *out)
+static __global__ void __launch_bounds__(256) k_stats(KParams p, const double *n_, const double *ux_, double *snap,
+                                                      int update_snap, double *partial)
 {
-    // one warp: lane l takes blocks l, l + 32, ...; then a fixed shuffle tree
-    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    stats_body(p, n_, ux_, snap, update_snap, partial, blockIdx.x, gridDim.x);
+}
+
+// one warp: lane l takes blocks l, l + 32, ...; then a fixed shuffle tree
+__device__ __forceinline__ void stats_final_body(const double *partial, int nblocks, double *out)
+{
+    if (threadIdx.x >= 32) return;
     double r[6] = {0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < nblocks; b += 32) {
         r[0] += partial[b * 6 + 0]; r[1] += partial[b * 6 + 1]; r[2] += partial[b * 6 + 2];
@@ -975,6 +981,11 @@ static __global__ void k_stats_final(const double *partial, int nblocks, double 
     }
     if (threadIdx.x == 0)
         for (int k = 0; k < 6; k++) out[k] = r[k];
+}
+
+static __global__ void k_stats_final(const double *partial, int nblocks, double *out)
+{
+    if (blockIdx.x == 0) stats_final_body(partial, nblocks, out);
 }
 
 // FP64 sum of the initial density over fluid nodes (for the default n_ref).

@@ -265,6 +265,18 @@ cudaError_t do_stats(const KParams &p, const DevBufs &d, int cur, int update_sna
     return cudaGetLastError();
 }
 
+cudaError_t do_batch_stats(const BatchLaunch &L, int parity, const StatSlot *slots, int nslots, int update_snap,
+                           double *res, int *st_out, cudaStream_t st, int64_t *launches)
+{
+    if (nslots < 1 || L.n_node_items < 1) return cudaSuccess;
+    const KBufs<S, T> *B = static_cast<const KBufs<S, T> *>(L.bufs[parity & 1]);
+    k_batch_stats_moments<S><<<L.n_node_items, kThreads, 0, st>>>(L.params, B, L.node_items, slots);
+    k_batch_stats<<<nslots * kStatBlocks, kThreads, 0, st>>>(L.params, slots, update_snap);
+    k_batch_stats_final<<<nslots, 32, 0, st>>>(slots, res, st_out);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
 void kbufs_fill(const DevBufs &d, int cur, void *out)
 {
     KBufs<S, T> b = typed(d, cur);
@@ -398,8 +410,9 @@ cudaError_t do_flow_step(const BatchLaunch &L, const FlowLaunch &F, cudaStream_t
 }
 
 static_assert(sizeof(KBufs<S, T>) <= kKBufsMaxBytes, "KBufs larger than its table slot");
-const Launchers kL = {do_prepare,  sizeof(KBufs<S, T>), kbufs_fill,    do_batch_step, do_init,   do_fields,
-                      do_moments,  do_population,       do_stats,      do_flow_ok,    do_flow_step, do_thermal};
+const Launchers kL = {do_prepare, sizeof(KBufs<S, T>), kbufs_fill, do_batch_step, do_init,      do_fields,
+                      do_moments, do_population,       do_stats,   do_batch_stats, do_flow_ok, do_flow_step,
+                      do_thermal};
 
 }  // namespace
 

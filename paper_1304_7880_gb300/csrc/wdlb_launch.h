@@ -65,6 +65,14 @@ struct BatchLaunch {
 
 constexpr size_t kKBufsMaxBytes = 256;   // room for one KBufs of any storage type in a table
 
+// FP64 statistics of a batch's slots in one set of launches (the residual
+// test): per slot its FP64 staging, u_x snapshot, partial sums and status
+// word (stage == nullptr: empty slot).
+struct StatSlot {
+    double *stage, *snap, *partial;
+    int *status;
+};
+
 // Persistent dataflow step of a batch (k_step_flow): per-slot item counts and
 // completion counters, the work counter and the abort flag in device memory
 // (done, next and abort_flag zeroed before each launch).
@@ -106,6 +114,11 @@ struct Launchers {
     // moments of buffer `cur`, then FP64 statistics into result[0..5] (see k_stats)
     cudaError_t (*stats)(const KParams &, const DevBufs &, int cur, int update_snap, cudaStream_t,
                          int64_t *launches);
+    // stats of every slot of the tables (input buffers of parity p) with the
+    // same partition and reduction order as `stats` per slot: results into
+    // res[6 slot ..], status words into st[slot]
+    cudaError_t (*batch_stats)(const BatchLaunch &, int parity, const StatSlot *slots, int nslots, int update_snap,
+                               double *res, int *st, cudaStream_t, int64_t *launches);
     // whether the persistent dataflow kernel serves these tables (one shell
     // group: tiled sigma 4, 8 x 8 x 4 bricks; tiled smeared density for all),
     // and its launch: F.nsteps time steps of every slot in one kernel

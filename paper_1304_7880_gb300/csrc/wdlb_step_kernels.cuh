@@ -200,4 +200,36 @@ __global__ void __launch_bounds__(tiled::threads_of(V), (tiled::blocks_per_sm<S2
     }
 }
 
+// The residual test's statistics for every slot of a table, in three
+// launches: FP64 moments over the slots' node blocks, then kStatBlocks blocks
+// per slot with the partition of the per-lattice k_stats, then one warp per
+// slot reducing its partial sums as k_stats_final does.
+template <class S>
+__global__ void __launch_bounds__(256) k_batch_stats_moments(const KParams *P, const KBufs<S, typename Store<S>::T> *B,
+                                                             const BatchItem *it, const StatSlot *ss)
+{
+    const BatchItem w = it[blockIdx.x];
+    const KParams p = P[w.slot];
+    const KBufs<S, typename Store<S>::T> b = B[w.slot];
+    double *stage = ss[w.slot].stage;
+    moments_body<S, true>(p, b, w.bx, stage, stage + p.N);
+}
+
+static __global__ void __launch_bounds__(256) k_batch_stats(const KParams *P, const StatSlot *ss, int update_snap)
+{
+    const int slot = blockIdx.x / kStatBlocks, blk = blockIdx.x % kStatBlocks;
+    const StatSlot t = ss[slot];
+    if (!t.stage) return;
+    const KParams p = P[slot];
+    stats_body(p, t.stage, t.stage + p.N, t.snap, update_snap, t.partial, blk, kStatBlocks);
+}
+
+static __global__ void k_batch_stats_final(const StatSlot *ss, double *res, int *st)
+{
+    const StatSlot t = ss[blockIdx.x];
+    if (!t.stage) return;
+    stats_final_body(t.partial, kStatBlocks, res + 6 * blockIdx.x);
+    if (threadIdx.x == 0) st[blockIdx.x] = *t.status;
+}
+
 }  // namespace wdlb
