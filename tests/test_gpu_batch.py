@@ -138,6 +138,34 @@ def test_batch_residuals_and_status(w):
     w.wdlb_batch_destroy(b)
 
 
+def test_batched_residual_test_equals_per_pore(w):
+    """The residual test of a batch whose tables are current (all pores in
+    three launches) gives the same bits as the per-pore path, which a batch
+    takes while its tables are stale (here after adding and removing a
+    pore): two identical batches, two rounds of steps and tests."""
+    def make():
+        b = w.wdlb_batch_create(len(PORES) + 1, 256 << 20, storage="f32")
+        for lat, sigma, walls, tau, g, nstar, seed in PORES:
+            n, u = pore_fields(lat, sigma, walls, nstar, seed)
+            w.wdlb_batch_add(b, lat, sigma, walls, tau, g, n, u)
+        return b
+    a, b = make(), make()
+    lat, sigma, walls, tau, g, nstar, seed = PORES[0]
+    dn, du = pore_fields(lat, sigma, walls, nstar, seed)
+    for _ in range(2):
+        w.wdlb_batch_step(a, 30)
+        w.wdlb_batch_step(b, 30)
+        ra, sa = w.wdlb_batch_residuals(a, 30)          # tables current: batched
+        w.wdlb_batch_remove(b, w.wdlb_batch_add(b, lat, sigma, walls, tau, g, dn, du))
+        rb, sb = w.wdlb_batch_residuals(b, 30)          # tables stale: per pore
+        k = len(PORES)
+        driven = [j for j, pr in enumerate(PORES) if pr[4][0] != 0]   # the undriven box has no flux
+        assert np.array_equal(ra[:k], rb[:k], equal_nan=True) and np.isfinite(ra[driven]).all()
+        assert np.array_equal(sa[:k], sb[:k]) and (sa[:k] == 0).all()
+    w.wdlb_batch_destroy(a)
+    w.wdlb_batch_destroy(b)
+
+
 def test_a_failing_pore_is_flagged_alone(w):
     """Per-pore failure detection.  A NaN in a pore's initial density (made on
     the host) is refused at admission; a pore whose state turns non-physical
