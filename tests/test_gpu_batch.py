@@ -152,7 +152,7 @@ def test_batched_residual_test_equals_per_pore(w):
     a, b = make(), make()
     lat, sigma, walls, tau, g, nstar, seed = PORES[0]
     dn, du = pore_fields(lat, sigma, walls, nstar, seed)
-    for _ in range(2):
+    for rnd in range(2):
         w.wdlb_batch_step(a, 30)
         w.wdlb_batch_step(b, 30)
         ra, sa = w.wdlb_batch_residuals(a, 30)          # tables current: batched
@@ -160,7 +160,8 @@ def test_batched_residual_test_equals_per_pore(w):
         rb, sb = w.wdlb_batch_residuals(b, 30)          # tables stale: per pore
         k = len(PORES)
         driven = [j for j, pr in enumerate(PORES) if pr[4][0] != 0]   # the undriven box has no flux
-        assert np.array_equal(ra[:k], rb[:k], equal_nan=True) and np.isfinite(ra[driven]).all()
+        assert np.array_equal(ra[:k], rb[:k], equal_nan=True)
+        assert rnd == 0 or np.isfinite(ra[driven]).all()    # the first test has no earlier flux: inf
         assert np.array_equal(sa[:k], sb[:k]) and (sa[:k] == 0).all()
     w.wdlb_batch_destroy(a)
     w.wdlb_batch_destroy(b)
