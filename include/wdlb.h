@@ -471,8 +471,7 @@ void wdlb_server_destroy(wdlb_server *s);
  * than WDLB_STATIC_MAX_NODES nodes, or sigma outside [1, 8], are rejected with
  * WDLB_ERR_ARG.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) on the current device and keeps it for the
- * later calls on that device; make that first call before any stream capture.
- * The kept address belongs to the device's current context: after a
+ * later calls on that device.  The kept address belongs to the device's current context: after a
  * cudaDeviceReset it is no longer valid.  All work is enqueued on `stream` (a
  * cudaStream_t, NULL = legacy default stream); the stencil tables are copied
  * from pageable host memory.  The call then waits for its work on `stream` to
