@@ -388,6 +388,7 @@ def run_serving(w, synth, np, rate, window_s, drain_s, max_active=48, tol=1e-8, 
             "solves_per_s": len(ok) / elapsed, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "backlog_at_end": info["queued"] + info["active"],
             "completed_mlups": node_steps / elapsed / 1e6, "server_mlups": info["node_steps"] / elapsed / 1e6,
+            "gpu_step_fraction": info["gpu_step_s"] / elapsed,
             "max_active": max_active, "collision": collision}
 
 

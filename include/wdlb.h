@@ -432,6 +432,10 @@ typedef struct {
     int64_t launches;
     double clock_s;
     int64_t node_steps;       /* lattice-node updates executed so far */
+    double gpu_step_s;        /* device time of the worker's blocks of time steps
+                                 (CUDA events on the batch's stream; the rest of
+                                 clock_s is admission, residual tests, retiring
+                                 and idle time)                                   */
 } wdlb_server_stats;
 
 /* opt as for wdlb_batch_create, except that opt->autotune is taken as 0: the
@@ -471,8 +475,8 @@ void wdlb_server_destroy(wdlb_server *s);
  * than WDLB_STATIC_MAX_NODES nodes, or sigma outside [1, 8], are rejected with
  * WDLB_ERR_ARG.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) on the current device and keeps it for the
- * later calls on that device.  The kept address belongs to the device's current context: after a
- * cudaDeviceReset it is no longer valid.  All work is enqueued on `stream` (a
+ * later calls on that device.  The kept address belongs to the device's
+ * current context: after a cudaDeviceReset it is no longer valid.  All work is enqueued on `stream` (a
  * cudaStream_t, NULL = legacy default stream); the stencil tables are copied
  * from pageable host memory.  The call then waits for its work on `stream` to
  * finish and reads back the status word its kernels set in the array:

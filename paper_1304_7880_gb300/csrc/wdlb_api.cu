@@ -1804,6 +1804,7 @@ struct wdlb_server {
     std::vector<wdlb_result> done;
     int64_t next_id = 1, submitted = 0, admitted = 0, completed = 0;
     int64_t node_steps = 0;       // lattice-node updates executed
+    double gpu_step_s = 0.0;      // device time of the blocks of time steps
     // the batch's counters as the worker last saw them (read under mu by
     // wdlb_server_info, which must not touch the batch the worker mutates)
     int32_t snap_active = 0;
@@ -1857,9 +1858,26 @@ void server_finish(wdlb_server *s, int slot, int32_t status, double residual)
     s->completed++;
 }
 
+// Two CUDA events of the worker thread, bracketing a block of time steps.
+struct StepTimer {
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    StepTimer()
+    {
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) e = nullptr;
+    }
+    ~StepTimer()
+    {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    bool ok() const { return ev[0] && ev[1]; }
+};
+
 void server_loop(wdlb_server *s)
 {
     cudaSetDevice(s->device);
+    StepTimer timer;
     std::vector<double> res(s->active.size()), tmp;
     std::vector<int32_t> st(s->active.size());
     for (;;) {
@@ -1943,12 +1961,23 @@ void server_loop(wdlb_server *s)
             std::lock_guard<std::mutex> lock(s->mu);
             s->node_steps += block_nodes * s->check_every;
         }
-        if (wdlb_batch_step(s->batch, s->check_every) != WDLB_OK ||
-            wdlb_batch_residuals(s->batch, s->check_every, res.data(), st.data()) != WDLB_OK) {
+        // the tables and the graph first, so that the events bracket device work only
+        bool timed = timer.ok();
+        if (s->batch->dirty && batch_build(s->batch) != WDLB_OK) timed = false;
+        if (timed && !s->batch->flow && batch_ensure_graph(s->batch) != WDLB_OK) timed = false;
+        if (timed) timed = cudaEventRecord(timer.ev[0], s->batch->stream) == cudaSuccess;
+        wdlb_status step_st = wdlb_batch_step(s->batch, s->check_every);
+        if (timed) timed = cudaEventRecord(timer.ev[1], s->batch->stream) == cudaSuccess;
+        if (step_st != WDLB_OK || wdlb_batch_residuals(s->batch, s->check_every, res.data(), st.data()) != WDLB_OK) {
             std::lock_guard<std::mutex> lock(s->mu);
             s->err = wdlb_batch_last_error(s->batch);
             for (size_t k = 0; k < s->active.size(); k++)
                 if (s->active[k].id) st[k] = WDLB_ERR_CUDA;
+        }
+        float ms = 0.f;   // the residual test synchronised the stream
+        if (timed && cudaEventElapsedTime(&ms, timer.ev[0], timer.ev[1]) == cudaSuccess) {
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->gpu_step_s += 1e-3 * double(ms);
         }
         for (size_t k = 0; k < s->active.size(); k++) {
             if (!s->active[k].id) continue;
@@ -2045,6 +2074,7 @@ wdlb_status wdlb_server_info(wdlb_server *s, wdlb_server_stats *info)
     info->launches = s->snap_launches;
     info->clock_s = server_now(s);
     info->node_steps = s->node_steps;
+    info->gpu_step_s = s->gpu_step_s;
     return WDLB_OK;
 }
 

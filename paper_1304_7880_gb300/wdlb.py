@@ -68,7 +68,8 @@ class wdlb_request(ctypes.Structure):
 class wdlb_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("active", ctypes.c_int64), ("pool_free", ctypes.c_uint64),
-                ("launches", ctypes.c_int64), ("clock_s", ctypes.c_double), ("node_steps", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("clock_s", ctypes.c_double), ("node_steps", ctypes.c_int64),
+                ("gpu_step_s", ctypes.c_double)]
 
 
 class wdlb_pore_stats(ctypes.Structure):

@@ -52,6 +52,8 @@ def test_server_results_equal_alone(w):
     info = w.wdlb_server_info(srv)
     w.wdlb_server_destroy(srv)
     assert len(results) == len(REQUESTS), info
+    # the device time of the blocks of steps, a part of the server's clock
+    assert 0 < info["gpu_step_s"] <= info["clock_s"], info
     for k, (lat, sigma, nstar, gx, seed) in enumerate(REQUESTS):
         r = results[k]
         assert r["status"] == 0 and r["residual"] < TOL
